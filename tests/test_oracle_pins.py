@@ -1,0 +1,407 @@
+"""Pins of the CPU oracle against closed forms, invariants and library routines.
+
+Every check here is independent of the oracle's own arithmetic: exact
+values a plain derivation gives, quadrature by another rule, dense or
+sparse library eigensolvers, physics limits (Lamb, rigid cavity acoustics,
+Newtonian gravity of a ball), so that a dropped term, a wrong sign or a
+transposed operand in the oracle fails one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+from scipy.special import spherical_jn
+from scipy.optimize import brentq
+
+from synth.mesh import layered_ball, tet_quality
+from synth.model import Model, config_ball, homogeneous_ball, layered_planet
+from oracle import p2, fem, eig, filtlan
+from oracle.lamb import lamb_modes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------ quadrature
+def _duffy_rule(n):
+    """Collapsed-cube Gauss rule on the unit tet {x,y,z >= 0, x+y+z <= 1}."""
+    g, w = np.polynomial.legendre.leggauss(n)
+    g = 0.5 * (g + 1.0)
+    w = 0.5 * w
+    pts, wts = [], []
+    for a, wa in zip(g, w):
+        for b, wb in zip(g, w):
+            for c, wc in zip(g, w):
+                x = a
+                y = b * (1 - a)
+                z = c * (1 - a) * (1 - b)
+                pts.append((x, y, z))
+                wts.append(wa * wb * wc * (1 - a) ** 2 * (1 - b))
+    return np.array(pts), np.array(wts)
+
+
+def _p2_shape(lam):
+    """P2 shape values at barycentric points (q, 4) -> (q, 10), by direct formula."""
+    out = [lam[:, i] * (2 * lam[:, i] - 1) for i in range(4)]
+    out += [4 * lam[:, i] * lam[:, j] for i, j in p2.EDGES]
+    return np.stack(out, 1)
+
+
+def test_reference_mass_by_quadrature():
+    pts, wts = _duffy_rule(6)
+    lam = np.column_stack([1 - pts.sum(1), pts])
+    phi = _p2_shape(lam)
+    Mq = np.einsum('q,qa,qb->ab', wts, phi, phi) / (1.0 / 6.0)   # per unit volume
+    assert np.allclose(p2.MASS_REF, Mq, atol=1e-14)
+
+
+def test_mass_row_sums_closed_form():
+    # int phi_vertex = -|K|/20, int phi_edge = |K|/5 for P2 on a tet
+    rs = p2.MASS_REF.sum(1)
+    assert np.allclose(rs[:4], -1 / 20, atol=1e-15)
+    assert np.allclose(rs[4:], 1 / 5, atol=1e-15)
+
+
+def test_jacobi_mass_spectrum_closed_form():
+    ev = np.sort(np.linalg.eigvals(np.diag(1 / np.diag(p2.MASS_REF)) @ p2.MASS_REF).real)
+    assert abs(ev[0] - 0.25) < 1e-13
+    assert abs(ev[-1] - (19 + np.sqrt(249.0)) / 8) < 1e-12
+    assert filtlan.MASS_LO == 0.25 and abs(filtlan.MASS_HI - ev[-1]) < 1e-12
+
+
+def test_grad_grad_by_quadrature_on_physical_tet():
+    rng = np.random.default_rng(5)
+    xyz = np.array([[0, 0, 0], [1.1, 0.1, 0], [0.2, 0.9, 0.1], [0.1, 0.3, 1.2]]) + rng.normal(0, 0.05, (4, 3))
+    tet = np.array([[0, 1, 2, 3]])
+    vol, grads = p2.tet_geometry(xyz, tet)
+    D = p2.grad_grad(vol, grads)[0]
+    C = p2.grad_val(vol, grads)[0]
+    # quadrature of the shape-function gradients via finite differences of the
+    # direct formula in physical coordinates (central, step 1e-5) and a Duffy rule
+    pts, wts = _duffy_rule(5)
+    J = np.stack([xyz[1] - xyz[0], xyz[2] - xyz[0], xyz[3] - xyz[0]], 1)
+    X = xyz[0] + pts @ J.T
+    Jinv = np.linalg.inv(J)
+
+    def shape_at(x):
+        r = (x - xyz[0]) @ Jinv.T
+        return _p2_shape(np.column_stack([1 - r.sum(1), r]))
+
+    h = 1e-5
+    G = np.stack([(shape_at(X + h * e) - shape_at(X - h * e)) / (2 * h) for e in np.eye(3)], 2)
+    phi = shape_at(X)
+    detJ = abs(np.linalg.det(J))
+    Dq = np.einsum('q,qap,qbr->apbr', wts * detJ, G, G)
+    Cq = np.einsum('q,qap,qb->apb', wts * detJ, G, phi)
+    assert np.allclose(D, Dq, atol=1e-8 * abs(D).max())
+    assert np.allclose(C, Cq, atol=1e-8 * abs(C).max())
+
+
+def test_nodal_grad_exact_for_quadratics():
+    xyz = np.array([[0, 0, 0], [1.0, 0.2, 0], [0.1, 1.1, 0], [0.2, 0.1, 0.9]])
+    tet10, _, edges = fem.p2_numbering(np.array([[0, 1, 2, 3]]), 4)
+    nodes = fem.p2_coords(xyz, edges)[tet10[0]]
+    f = lambda x: np.stack([x[:, 0] * x[:, 1], x[:, 2] ** 2, x[:, 0]], 1)     # quadratic field
+    df = lambda x: np.stack([np.stack([x[:, 1], np.zeros(len(x)), np.ones(len(x))], 1),
+                             np.stack([x[:, 0], np.zeros(len(x)), np.zeros(len(x))], 1),
+                             np.stack([np.zeros(len(x)), 2 * x[:, 2], np.zeros(len(x))], 1)], 1)
+    _, grads = p2.tet_geometry(xyz, np.array([[0, 1, 2, 3]]))
+    g = p2.nodal_grad(grads, f(nodes)[None])[0]                # [a, p, j]
+    assert np.allclose(g, df(nodes), atol=1e-12)
+
+
+# ------------------------------------------------------------ mesh
+def test_mesh_conforming_and_quality():
+    m = layered_ball(radii=(0.19, 0.55, 1.0), h=0.12, fluid_layers=(1,), seed=4)
+    assert tet_quality(m.xyz, m.tet).min() > 0.08
+    f = np.sort(np.concatenate([m.tet[:, [1, 2, 3]], m.tet[:, [0, 2, 3]],
+                                m.tet[:, [0, 1, 3]], m.tet[:, [0, 1, 2]]]), 1)
+    _, cnt = np.unique(f, axis=0, return_counts=True)
+    assert cnt.max() == 2
+    # boundary faces lie on the unit sphere (vertices exactly on it)
+    bf = np.unique(f, axis=0, return_counts=True)
+    bverts = np.unique(bf[0][bf[1] == 1])
+    assert np.allclose(np.linalg.norm(m.xyz[bverts], axis=1), 1.0, atol=1e-12)
+
+
+# ------------------------------------------------------------ elastic ball
+@pytest.fixture(scope="module")
+def ball():
+    w = config_ball()
+    S = fem.assemble(w.mesh, w.model)
+    K, M = eig.pencil_dense(S)
+    lam, X = eig.all_eigs(K, M)
+    return w, S, K, M, lam, X
+
+
+def _rigid_modes(S):
+    x = S.node_xyz[S.dm.u_p2]
+    Nu = len(x)
+    out = []
+    for c in range(3):
+        v = np.zeros((Nu, 3))
+        v[:, c] = 1
+        out.append(v.ravel())
+    for axis in np.eye(3):
+        out.append(np.cross(axis, x).ravel())
+    return np.stack(out, 1)
+
+
+def test_ball_matrices_symmetric_spd(ball):
+    _, S, K, M, _, _ = ball
+    assert abs(K - K.T).max() <= 1e-14 * abs(K).max()
+    assert abs(M - M.T).max() <= 1e-15 * abs(M).max()
+    assert np.linalg.eigvalsh(M).min() > 0
+    # total mass: 1^T M_rho 1 = sum rho |K|
+    vol, _ = p2.tet_geometry(w_xyz := ball[0].mesh.xyz, ball[0].mesh.tet)
+    assert np.isclose(S.M_rho.sum(), (ball[0].model.rho * vol).sum(), rtol=1e-13)
+
+
+def test_ball_rigid_null_space(ball):
+    _, S, K, M, lam, X = ball
+    Rm = _rigid_modes(S)
+    assert np.abs(K @ Rm).max() <= 1e-12 * abs(K).max()
+    lmax = lam[-1]
+    zero = np.abs(lam) <= 1e-10 * lmax
+    assert zero.sum() == 6
+    # the zero eigenvectors span the rigid motions
+    Q, _ = np.linalg.qr(Rm)
+    Z = X[:, zero]
+    resid = Z - Q @ (Q.T @ Z)
+    assert np.linalg.norm(resid) <= 1e-8 * np.linalg.norm(Z)
+
+
+def test_ball_slice_count_and_multiplets(ball):
+    _, _, _, _, lam, _ = ball
+    om = np.sqrt(np.clip(lam, 0, None))
+    assert ((om >= 0) & (om <= 3.0)).sum() == 16
+    # two 5-fold groups above the zero modes: 0T2 then 0S2
+    t2 = om[6:11]
+    s2 = om[11:16]
+    assert t2.max() - t2.min() < 0.03 and s2.max() - s2.min() < 0.03
+    assert t2.max() < s2.min()
+
+
+def test_lamb_golden_matches_closed_form():
+    with open(os.path.join(GOLDEN, "lamb_ball.json")) as f:
+        g = json.load(f)
+    modes = lamb_modes(6.0)
+    assert [m[1] for m in modes] == [m["label"] for m in g["modes"]]
+    assert np.allclose([m[0] for m in modes], [m["omega"] for m in g["modes"]], rtol=1e-12)
+
+
+def test_lamb_toroidal_is_first_root_of_bessel_relation():
+    # independent check of the toroidal relation: (l-1) j_l - x j_{l+1}
+    # equals x^2 d/dx (j_l / x) (spherical-Bessel identity), so its roots are
+    # the stationary points of j_l(x)/x
+    f = lambda x: (spherical_jn(2, x + 1e-6) / (x + 1e-6) - spherical_jn(2, x - 1e-6) / (x - 1e-6))
+    x0 = brentq(f, 1.0, 3.0)
+    assert abs(x0 - lamb_modes(3.0)[0][0]) < 1e-6
+
+
+def test_ball_converges_to_lamb():
+    """0T2 and 0S2 multiplet means approach Lamb's values under refinement."""
+    exact = {m[1]: m[0] for m in lamb_modes(3.0)}
+    errs = []
+    for h in (0.45, 0.3):
+        mesh, model = homogeneous_ball(h=h, seed=1)
+        S = fem.assemble(mesh, model)
+        w, _ = eig.eigs_near(S, 2.55 ** 2, 16)
+        om = np.sort(np.sqrt(np.clip(w, 0, None)))
+        om = om[om > 1.0][:10]
+        errs.append((om[:5].mean() / exact["0T2"] - 1, om[5:].mean() / exact["0S2"] - 1))
+    (t0, s0), (t1, s1) = errs
+    assert 0 < t1 < t0 < 0.06 and 0 < s1 < s0 < 0.06
+    assert t1 < 0.02 and s1 < 0.02
+
+
+# ------------------------------------------------------------ fluid pieces
+def _fluid_ball(h, vp=1.3, rho=1.0):
+    m = layered_ball(radii=(1.0,), h=h, fluid_layers=(0,), seed=3)
+    nt = m.nt
+    mdl = Model(rho=np.full(nt, rho), lam=np.full(nt, rho * vp * vp), mu=np.zeros(nt),
+                N2=np.zeros(nt), G=0.0, Omega=np.zeros(3))
+    return fem.assemble(m, mdl), vp
+
+
+def test_fluid_ball_rigid_cavity_acoustics():
+    """A fluid ball without gravity is a rigid-walled acoustic cavity.
+
+    The weak pressure constraint without a free-surface term imposes
+    u.nu = 0 on the boundary, so the nonzero modes tend to
+    omega = Vp x with j_l'(x) = 0 (l = 1: x = 2.0816, l = 2: 3.3421).
+    """
+    S, vp = _fluid_ball(0.3)
+    w, _ = eig.eigs_near(S, (2.7 * vp) ** 2, 12)
+    x = np.sqrt(np.clip(w, 0, None)) / vp
+    x = np.sort(x[x > 1.0])
+    r1 = brentq(lambda t: spherical_jn(1, t, derivative=True), 1.5, 2.5)
+    r2 = brentq(lambda t: spherical_jn(2, t, derivative=True), 3.0, 3.6)
+    assert np.allclose(x[:3], r1, rtol=0.02) and (x[:3] > r1).all()
+    assert np.allclose(x[3:8], r2, rtol=0.02) and (x[3:8] > r2).all()
+
+
+def test_fluid_pressure_blocks_closed_forms():
+    S, vp = _fluid_ball(0.45)
+    kap = vp * vp
+    vol = S.M_rho.sum()          # rho = 1
+    assert np.isclose(S.A_p.sum(), -vol / kap, rtol=1e-12)
+    # A_dg: int v.grad p for v = e_j and p = a.x (exact in P2)
+    a = np.array([0.3, -1.2, 0.7])
+    p = S.node_xyz[np.nonzero(S.dm.pnode >= 0)[0]] @ a
+    for j in range(3):
+        v = np.zeros(S.n)
+        v[j::3] = 1.0
+        assert np.isclose(v @ (S.E_G @ p), a[j] * vol, rtol=1e-12)
+
+
+def test_layered_rigid_modes_without_gravity():
+    """Solid-fluid-solid ball without gravity: the 6 rigid motions stay exact
+    zero modes of K_eff, which needs E_FS and A_dg with consistent signs
+    (the fluid-side and solid-side boundary integrals cancel)."""
+    mesh, model = layered_planet(h=0.25, seed=7)
+    model.G = 0.0
+    S = fem.assemble(mesh, model)
+    Rm = _rigid_modes(S)
+    assert np.abs(S.E_G.T @ Rm).max() <= 1e-12 * abs(S.E_G).max()
+    K = fem.k_eff_dense(S)
+    assert np.abs(K @ Rm).max() <= 1e-10 * abs(K).max()
+    # and E_FS alone does not vanish on them (the cancellation is real)
+    fs_rows = np.zeros(S.n, bool)
+    fs_rows[:3 * int((S.dm.unode_solid >= 0).sum())] = True
+    assert np.abs(S.E_G[fs_rows].T @ Rm[fs_rows]).max() > 1e-3
+
+
+def test_cowling_homogeneous_ball_rigid_motions():
+    """Cowling approximation (reference field fixed, no S(u)): a homogeneous
+    ball translated rigidly oscillates in its own potential well with
+    omega^2 = (4/3) pi G rho, and rigid rotations cost no energy. This pins
+    the signs and weights of all three symmetrised gravity volume terms."""
+    mesh, model = homogeneous_ball(h=0.3, seed=1)
+    model.G = 1.0 / np.pi
+    S = fem.assemble(mesh, model)
+    K = fem.k_eff_dense(S)
+    M = S.M.toarray()
+    Rm = _rigid_modes(S)
+    ray = np.diag(Rm.T @ K @ Rm) / np.diag(Rm.T @ M @ Rm)
+    assert np.allclose(ray[:3], 4.0 / 3.0 * np.pi * model.G * 1.0, rtol=0.01)
+    assert np.abs(ray[3:]).max() < 0.01
+    lam = eig.all_eigs(K, M)[0]
+    assert np.allclose(lam[3:6], 4.0 / 3.0, rtol=0.01)
+
+
+def test_layered_cowling_spectrum_structure():
+    """Three-layer planet, Cowling: K_eff symmetric; the only clearly
+    negative modes are the three inner-core translations (a dense inner core
+    in a lighter fluid has no self-gravity restoring force without S(u));
+    a large near-zero cluster comes from the fluid (essential spectrum)."""
+    mesh, model = layered_planet(h=0.25, seed=7)
+    S = fem.assemble(mesh, model)
+    assert abs(S.A_G - S.A_G.T).max() <= 1e-13 * abs(S.A_G).max()
+    K = fem.k_eff_dense(S)
+    lam, X = eig.all_eigs(K, S.M.toarray())
+    neg = np.nonzero(lam < -0.01)[0]
+    assert len(neg) == 3
+    ns = int((S.dm.unode_solid >= 0).sum())
+    r = np.linalg.norm(S.node_xyz[S.dm.u_p2], axis=1)
+    ic = (r < 0.19 + 1e-9) & (np.arange(len(r)) < ns)
+    md = S.M_rho.diagonal()
+    for i in neg:
+        u = X[:, i].reshape(-1, 3)
+        e = (u * u).sum(1) * md
+        assert e[ic].sum() > 0.9 * e.sum()
+    assert (np.abs(lam) < 0.01).sum() > 0.2 * S.dm.Np
+
+
+def test_gravity_direct_summation_homogeneous_ball():
+    """Point-mass direct summation (Sec. 5.1) against Newton for a ball.
+
+    Outside: the monopole -G M x/|x|^3 to 5e-4. Inside the field is
+    -(4/3) pi G rho x; point masses at the barycentres carry an O(h)
+    pointwise error from the nearest masses, so the pin is the radially
+    averaged interior field (a few per cent) and its decrease under
+    refinement.
+    """
+    G = 1.0 / np.pi
+    far = np.array([[2.0, 0.0, 0.0], [0.0, -3.0, 1.0]])
+    errs = []
+    for h in (0.3, 0.2):
+        mesh, model = homogeneous_ball(h=h, seed=1)
+        vol, _ = p2.tet_geometry(mesh.xyz, mesh.tet)
+        Mtot = vol.sum()
+        gf = fem.gravity_direct(far, mesh.xyz, mesh.tet, model.rho, G)
+        ex = -G * Mtot * far / np.linalg.norm(far, axis=1, keepdims=True) ** 3
+        assert np.abs(gf - ex).max() <= 5e-4 * np.abs(ex).max()
+        x = mesh.xyz[np.linalg.norm(mesh.xyz, axis=1) < 0.8]
+        x = x[np.linalg.norm(x, axis=1) > 0.1]
+        g = fem.gravity_direct(x, mesh.xyz, mesh.tet, model.rho, G)
+        ratio = -np.einsum('ij,ij->i', g, x) / ((4.0 / 3.0) * np.pi * G * np.einsum('ij,ij->i', x, x))
+        assert abs(ratio.mean() - 1.0) < 0.05
+        errs.append(np.sqrt(np.mean((g + (4.0 / 3.0) * np.pi * G * x) ** 2)))
+    assert errs[1] < errs[0]
+
+
+# ------------------------------------------------------------ filter steps
+def test_jackson_and_step_coeffs_vs_numpy_chebval():
+    gam, c, e = filtlan.filter_coeffs(0.0, 10.0, 2.0, 4.0, 60)
+    assert filtlan.jackson(60)[0] == pytest.approx(1.0)
+    t = np.linspace(-1, 1, 101)
+    assert np.allclose(filtlan.cheb_eval(gam, t), np.polynomial.chebyshev.chebval(t, gam), atol=1e-13)
+    p = filtlan.cheb_eval(gam, (np.array([0.5, 3.0, 9.0]) - c) / e)
+    assert p[1] > 0.9 and p[0] < 0.05 and p[2] < 0.05
+
+
+def test_cheb_solve_converges_to_direct_solve_within_bound(ball):
+    _, S, _, _, _, _ = ball
+    rng = np.random.default_rng(0)
+    W = rng.standard_normal((S.n, 3))
+    exact = spla.spsolve(S.M.tocsc(), W)
+    dinv = 1.0 / S.M.diagonal()
+    lo, hi = filtlan.MASS_LO, filtlan.MASS_HI
+    rate = (np.sqrt(hi / lo) - 1) / (np.sqrt(hi / lo) + 1)
+    Mm = S.M
+    for k in (10, 20, 40):
+        X = filtlan.cheb_solve(Mm, dinv, W, k)
+        E = X - exact
+        # error in the M-norm bounded by 2 rate^k times the initial error
+        e_now = np.sqrt(np.einsum('ij,ij->j', E, Mm @ E))
+        e_0 = np.sqrt(np.einsum('ij,ij->j', exact, Mm @ exact))
+        assert (e_now <= 2 * rate ** k * e_0 * (1 + 1e-9)).all()
+    X = filtlan.cheb_solve(Mm, dinv, W, 80)
+    assert np.abs(X - exact).max() <= 1e-12 * np.abs(exact).max()
+
+
+def test_filter_apply_matches_spectral_evaluation(ball):
+    """Recurrence == p((B - c)/e) Y evaluated through an eigendecomposition."""
+    _, S, K, M, _, _ = ball
+    op = filtlan.Operator(S, k_M=12)
+    n = S.n
+    PM = op.Minv(np.eye(n))
+    B = PM @ K
+    wB, VB = np.linalg.eig(B)
+    gam, c, e = filtlan.filter_coeffs(-1.0, 5000.0, 0.0, 9.0, 30)
+    Y = np.random.default_rng(1).standard_normal((n, 2))
+    Z = filtlan.filter_apply(op, gam, c, e, Y)
+    pw = filtlan.cheb_eval(gam, ((wB - c) / e).real)
+    Zs = (VB @ (pw[:, None] * np.linalg.solve(VB, Y))).real
+    assert np.abs(Z - Zs).max() <= 1e-9 * np.abs(Zs).max()
+
+
+def test_lanczos_slice_matches_dense(ball):
+    w, S, K, M, lam, _ = ball
+    op = filtlan.Operator(S, k_M=40)
+    lo, hi = filtlan.spectrum_bounds(op, S.n)
+    assert hi >= lam[-1] and lo <= lam[0]
+    lam_lo, lam_hi = -1e-8 * hi, 9.0
+    got, X, res, info = filtlan.lanczos_slice(op, lam_lo, lam_hi, 100, 8, 16, bounds=(lo, hi))
+    ref = lam[(lam >= lam_lo) & (lam <= lam_hi)]
+    assert len(got) == len(ref) == 16
+    big = np.abs(ref) > 1e-10 * lam[-1]
+    assert np.allclose(got[big], ref[big], rtol=1e-10)
+    assert np.abs(got[~big]).max() <= 1e-10 * lam[-1]
+    assert res.max() <= 1e-6
+    # cross-check the residual with the dense pencil
+    r2 = eig.residuals(K, M, got, X, floor=filtlan.residual_floor(lam_lo, lam_hi))
+    assert r2.max() <= 1e-6
