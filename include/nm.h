@@ -1,0 +1,280 @@
+/*
+ * nm.h - C ABI of the GB300 filtered-Lanczos normal-mode solver.
+ *
+ * What it solves. Interior eigenpairs of the continuous-Galerkin P2
+ * discretisation of the elastic(-gravitational) equations on a tetrahedral
+ * planet mesh (paper Sec. 4, Table of matrix formulae, Appendix A):
+ *
+ *     K_eff u = lambda M u,  lambda = omega^2 in a slice [lo, hi]      (eq. gep)
+ *     K_eff = A_G - E_G A_p^{-1} E_G^T      (Cowling operator, eq. cowling)
+ *
+ * by a Chebyshev polynomial filter and block Lanczos (Sec. 6.2, which
+ * touches A, M and M^{-1} only through matrix-vector products), and, for
+ * a rotating body, the projection of the quadratic problem onto the Ritz
+ * vectors (eq. sublinear0, Sec. 7).
+ *
+ * Conventions shared by every call.
+ *  - Return value: NM_OK (0) or one of the NM_E* codes below. Nothing
+ *    aborts, traps or throws across the ABI; nm_last_error() gives text.
+ *  - Objects created by the library (nm_ctx, nm_problem, nm_result) are
+ *    owned by it and freed only by the matching *_destroy / *_free call.
+ *  - Device pointers passed in are borrowed: the caller allocates them and
+ *    keeps them alive for the duration of the call (until the stream
+ *    reaches the call's last kernel for the asynchronous calls).
+ *  - Blocks of vectors are ROW-MAJOR with a leading dimension: a block of b
+ *    vectors over the n = 3 Nu displacement dofs is an (n x b) array with
+ *    element (dof i, vector j) at X[i * ld + j], ld >= b. Dof i is
+ *    component (i % 3) of u-node (i / 3) in the library's INTERNAL node
+ *    order (see nm_problem_unodes); pressure-sized blocks likewise over
+ *    the Np pressure nodes.
+ *  - Streams: calls that take a cudaStream_t (passed as void*) only
+ *    enqueue work on it; NULL means the legacy default stream. Calls
+ *    without a stream argument (assembly, lanczos_slice, ritz) run on the
+ *    problem's own stream and return after synchronising it.
+ *  - Precision: NM_F64 computes in double, NM_F32 in float (values and
+ *    accumulators), for the filter-path calls that take an nm_prec.
+ */
+#ifndef NM_H
+#define NM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    NM_OK = 0,
+    NM_EINVAL = 1,        /* invalid argument or malformed mesh             */
+    NM_ENOMEM = 2,        /* device or host allocation failed               */
+    NM_ENOTCONV = 3,      /* solver stopped without converging              */
+    NM_ECUDA = 4,         /* a CUDA / cuBLAS / cuSOLVER call failed          */
+    NM_ETIMEOUT = 5,      /* a bounded device wait ran out                  */
+    NM_EUNSUPPORTED = 6   /* option not supported by this build              */
+};
+
+/* NM_F64: every step in double. NM_F32: the whole filter recurrence in
+ * float. NM_MIXED: double recurrence and K_eff SpMMs; each inner solve (mass
+ * and fluid pressure) is k steps of float semi-iteration, one double
+ * residual r = w - A x (float iterate, double values and sums), and k more
+ * float steps on r, so the applied inverse is accurate to ~(2 rho^k)^2
+ * while its vectors carry double rounding only. Blocks are double. */
+typedef enum { NM_F64 = 0, NM_F32 = 1, NM_MIXED = 2 } nm_prec;
+typedef enum { NM_UNIT_OMEGA = 0, NM_UNIT_OMEGA2 = 1 } nm_unit;
+typedef enum { NM_RITZ_PENCIL = 0, NM_RITZ_ROTATING = 1 } nm_ritz_mode;
+
+/* flags of nm_model */
+#define NM_GRAVITY       1u   /* include the reference-gravity terms of A_G and E_G */
+#define NM_CENTRIFUGAL   2u   /* g' = g - grad psi: not supported (NM_EUNSUPPORTED) */
+
+typedef struct nm_ctx nm_ctx;
+typedef struct nm_problem nm_problem;
+typedef struct nm_result nm_result;
+
+/* Mesh (host memory, read during nm_assemble only).
+ * xyz[3*nv] vertex coordinates; tet[4*nt] vertex ids (0-based, any
+ * orientation, non-degenerate); region[nt]: 0 solid, 1 fluid. */
+typedef struct {
+    int64_t nv;
+    const double* xyz;
+    int64_t nt;
+    const int32_t* tet;
+    const uint8_t* region;
+} nm_mesh;
+
+/* Model (host memory, read during nm_assemble only). Per-tet constants
+ * (Appendix A samples rho, c, kappa, N^2 per element): rho > 0, Lame
+ * lambda and mu (fluid: mu = 0, kappa = lambda), N2 (fluid buoyancy).
+ * gprime: optional reference field g' at the CANONICAL P2 nodes (3 * n_p2
+ * doubles, canonical order as in nm_problem_unodes); NULL = computed by
+ * direct summation over tet point masses with constant G (Sec. 5.1).
+ * Omega: rotation vector used by NM_RITZ_ROTATING (c_r, eq. rotationQ). */
+typedef struct {
+    const double* rho;
+    const double* lam;
+    const double* mu;
+    const double* N2;
+    const double* gprime;
+    double G;
+    double Omega[3];
+    uint32_t flags;
+} nm_model;
+
+typedef struct {
+    int64_t nv, nt;
+    int64_t n_p2;      /* P2 nodes: vertices + edges                       */
+    int64_t Nu;        /* displacement nodes (fluid-solid nodes twice)      */
+    int64_t n;         /* displacement dofs = 3 Nu                          */
+    int64_t Np;        /* pressure nodes (0 without fluid)                  */
+    int64_t nnz_u;     /* stored blocks of A_G (= stored entries of M_rho)  */
+    int64_t nnz_p;     /* stored entries of A_p                             */
+    int64_t nnz_e;     /* stored 3x1 blocks of E_G                          */
+    int64_t n_fs;      /* fluid-solid interface faces                       */
+} nm_problem_info;
+
+/* Filter for nm_filter_apply: Z = sum_{k=0..degree} gamma[k] T_k(B) Y with
+ * B = (P_M K_eff - c)/e, T_k Chebyshev polynomials, P_M ~ M^{-1} by k_M
+ * steps of Jacobi-preconditioned Chebyshev semi-iteration with bounds
+ * [m_lo, m_hi] of D^{-1} M, and the A_p^{-1} of K_eff by k_P steps with the
+ * same bounds. gamma: host array of degree+1 doubles. */
+typedef struct {
+    int32_t degree;
+    const double* gamma;
+    double c, e;
+    int32_t k_M, k_P;
+    double m_lo, m_hi;   /* 0, 0: the P2 element bounds [1/4, (19+sqrt 249)/8] */
+} nm_filter;
+
+typedef struct {
+    int32_t block;        /* Lanczos block width b (1..64)                   */
+    int32_t degree;       /* filter degree d                                 */
+    int32_t k_M, k_P;     /* inner semi-iteration steps (0: 57 / 57)         */
+    int32_t max_blocks;   /* basis size limit in blocks                      */
+    int32_t check_every;  /* Rayleigh-Ritz convergence test period (blocks)  */
+    nm_prec filter_prec;  /* precision of the filter SpMMs and mass solves   */
+    double tol;           /* residual tolerance (default 1e-6)               */
+    uint64_t seed;        /* start block seed (counter-based Philox-4x32-10) */
+    const double* start;  /* optional device start block (n x block, ld=block); NULL: drawn from seed */
+    int32_t bounds_steps; /* Lanczos steps for the spectrum bounds (0: 40)   */
+} nm_slice_opts;
+
+/* ---- context ---------------------------------------------------------- */
+/* Create a context on CUDA device `device` (cudaSetDevice is called). */
+int nm_ctx_create(int device, nm_ctx** out);
+int nm_ctx_destroy(nm_ctx* ctx);
+/* Last error message of the context (or of the most recent failing call
+ * when ctx is NULL). Valid until the next call on that context. */
+const char* nm_last_error(const nm_ctx* ctx);
+
+/* ---- assembly (Sec. 4.2, Appendix A) ----------------------------------
+ * Builds every matrix on the device and keeps it resident: A_G as a 3x3
+ * block CSR over the u-nodes, M_rho as a scalar CSR on the same graph,
+ * -A_p as a scalar CSR over the pressure nodes, E_G as 3x1 and E_G^T as
+ * 1x3 block CSR. NM_EINVAL on malformed input (ids out of range,
+ * degenerate tet, rho <= 0, fluid kappa <= 0). */
+int nm_assemble(nm_ctx* ctx, const nm_mesh* mesh, const nm_model* model, nm_problem** out);
+int nm_problem_free(nm_problem* prob);
+int nm_problem_get_info(const nm_problem* prob, nm_problem_info* info);
+
+/* Node maps (host outputs, caller-allocated):
+ * canon[Nu]: the canonical u-node id of each internal u-node. Canonical
+ *   order: P2 nodes are the mesh vertices 0..nv-1 then every edge once in
+ *   lexicographic (min vertex, max vertex) order; u-nodes are the P2 nodes
+ *   touching a solid tet in increasing P2 id, then those touching a fluid
+ *   tet in increasing P2 id.
+ * p2[Nu]: the P2 node id of each internal u-node (may be NULL).
+ * pcanon[Np]: the canonical pressure node of each internal pressure node
+ *   (fluid P2 nodes in increasing P2 id; may be NULL). */
+int nm_problem_unodes(const nm_problem* prob, int64_t* canon, int64_t* p2, int64_t* pcanon);
+
+/* Copy an assembled matrix to host CSR in the library's internal order.
+ * which: 0 A_G (3x3 blocks, vals 9 per block, row-major), 1 M_rho (1 per
+ * entry), 2 -A_p, 3 E_G (3x1 blocks), 4 E_G^T (1x3 blocks). Pass NULL
+ * buffers to query sizes in *nrows / *nnz; then rowptr[nrows+1],
+ * col[nnz], vals[nnz * block entries]. */
+int nm_problem_export(const nm_problem* prob, int which, int64_t* nrows, int64_t* nnz,
+                      int64_t* rowptr, int32_t* col, double* vals);
+
+/* Reference field g' at the internal u-nodes (host out, 3*Nu doubles). */
+int nm_problem_gravity(const nm_problem* prob, double* g);
+
+/* ---- operator pieces (A, M, M^{-1} as matrix-vector products, Sec. 6.2) */
+/* Y = K_eff X. The fluid Schur term uses k_P steps (0: 80, effectively
+ * exact in FP64) of the Jacobi-Chebyshev solve for -A_p. X, Y device. */
+int nm_apply_K(nm_problem* prob, const void* X, int64_t ldx, void* Y, int64_t ldy, int b,
+               int k_P, nm_prec prec, void* stream);
+/* Y = M X (M = M_rho (x) I_3). */
+int nm_apply_M(nm_problem* prob, const void* X, int64_t ldx, void* Y, int64_t ldy, int b,
+               nm_prec prec, void* stream);
+/* X = P_M W: k_M steps of Jacobi-preconditioned Chebyshev semi-iteration
+ * for M X = W with bounds [m_lo, m_hi] (0, 0: the P2 element bounds). */
+int nm_solve_M(nm_problem* prob, int k_M, double m_lo, double m_hi, const void* W, int64_t ldw,
+               void* X, int64_t ldx, int b, nm_prec prec, void* stream);
+/* Y = R X with R = M_rho (x) [Omega]_x (Coriolis form c_r, eq. rotationQ;
+ * the paper's R_s, R_f with the Levi-Civita symbol contracted with Omega). */
+int nm_apply_R(nm_problem* prob, const void* X, int64_t ldx, void* Y, int64_t ldy, int b,
+               nm_prec prec, void* stream);
+
+/* ---- slice set-up ------------------------------------------------------
+ * Store the target interval (eq. freq): unit NM_UNIT_OMEGA takes angular
+ * frequencies (lambda = omega^2; a negative lo means lambda_lo = -lo^2 is
+ * NOT used: lo < 0 is clamped to -1e-8 * lambda_max at solve time),
+ * NM_UNIT_OMEGA2 takes lambda directly. */
+int nm_set_interval(nm_problem* prob, double lo, double hi, nm_unit unit);
+/* Spectrum bounds of B = P_M K_eff (Lanczos with `steps` steps, FP64):
+ * lam_hi = 1.01 (theta_max + |resid|), lam_lo = min(0, theta_min) - 1e-6 lam_hi
+ * (the bottom Ritz residual is not subtracted: it is large at the clustered
+ * low end and would cost filter resolution where low slices sit). */
+int nm_spectrum_bounds(nm_problem* prob, int steps, int k_M, uint64_t seed, double* lam_lo,
+                       double* lam_hi);
+/* Jackson-damped Chebyshev coefficients of the indicator of [xi, eta]
+ * mapped from [lam_lo, lam_hi] to [-1, 1] (host math). gamma[degree+1],
+ * c, e out. */
+int nm_filter_design(double lam_lo, double lam_hi, double xi, double eta, int degree,
+                     double* gamma, double* c, double* e);
+
+/* ---- hot path ------------------------------------------------------------
+ * Z = p(B) Y for a block of b vectors (row-major, device). Scratch for the
+ * recurrence is owned by the problem and reused across calls (allocated
+ * on first use for the largest b seen). prec selects the arithmetic of the
+ * whole recurrence; X and Y then hold doubles (NM_F64) or floats (NM_F32). */
+int nm_filter_apply(nm_problem* prob, const nm_filter* f, const void* Y, int64_t ldy, void* Z,
+                    int64_t ldz, int b, nm_prec prec, void* stream);
+
+/* Filtered block Lanczos for every eigenpair with lambda in the interval
+ * set by nm_set_interval (Sec. 6.2), followed by an FP64 Rayleigh-Ritz of
+ * the pencil and FP64 residuals. NM_ENOTCONV if max_blocks is reached
+ * before every eigenpair in the slice passes tol (the result is still
+ * returned). */
+int nm_lanczos_slice(nm_problem* prob, const nm_slice_opts* opts, nm_result** out);
+
+/* Rayleigh-Ritz on a caller basis V (device, n x m, row-major, ld ldv,
+ * FP64). NM_RITZ_PENCIL: Ritz pairs of (K_eff, M) on span V inside the
+ * interval. NM_RITZ_ROTATING: V must hold M-orthonormal Ritz vectors X_e
+ * with Ritz values lam_e (host, m doubles, all > 0); solves the projected
+ * rotating problem (eq. sublinear0) and keeps omega in [w_lo, w_hi] of
+ * the interval (unit omega). */
+int nm_ritz(nm_problem* prob, nm_ritz_mode mode, const double* V, int64_t ldv, int m,
+            const double* lam_e, nm_result** out);
+
+/* ---- kernel timing --------------------------------------------------------
+ * With profiling enabled, every filter degree brackets its launch
+ * sequences with CUDA events on the launching stream: kind 0 = the mass
+ * solve's semi-iteration steps (k_M - 1 back-to-back launches of the
+ * fused M_rho SpMM + update kernel), kind 1 = the K_eff application
+ * (E_G^T SpMM, the pressure semi-iteration, the A_G (+ E_G) SpMM).
+ * nm_profile_read synchronises the problem's recorded streams and returns
+ * the launch count and summed device milliseconds of a kind since the
+ * last reset. Profiling adds two events per region and degree. */
+int nm_profile(nm_problem* prob, int enable, int reset);
+/* Number of kernels this library has launched in the process so far
+ * (every launch of every entry point, all devices). */
+uint64_t nm_kernel_launches(void);
+int nm_profile_read(nm_problem* prob, int kind, int64_t* launches, double* ms);
+
+/* ---- results ------------------------------------------------------------ */
+typedef struct {
+    int64_t k;            /* eigenpairs returned                              */
+    int64_t n;            /* rows of the eigenvector block                    */
+    int32_t complex_vectors; /* 1: X holds complex128 (rotating), else float64 */
+    int32_t blocks;       /* Lanczos blocks used                               */
+    int64_t m;            /* basis columns used                                */
+    int64_t filter_applications; /* vectors filtered (blocks x b)             */
+    double lam_lo, lam_hi;/* spectrum bounds used                               */
+    double seconds;       /* wall time of the call                             */
+    double seconds_filter;/* part spent in nm_filter_apply                     */
+} nm_result_info;
+
+int nm_result_get_info(const nm_result* res, nm_result_info* info);
+/* Host copies: lambda[k] (lambda = omega^2; rotating: omega), resid[k]. */
+int nm_result_values(const nm_result* res, double* lambda, double* resid);
+/* Device pointer of the eigenvector block (n x k row-major, ld = k), owned
+ * by the result. */
+const void* nm_result_vectors(const nm_result* res);
+int nm_result_free(nm_result* res);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NM_H */

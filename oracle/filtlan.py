@@ -60,13 +60,26 @@ def cheb_solve(A, dinv, W, k, lo=MASS_LO, hi=MASS_HI):
     return x
 
 
-class Operator:
-    """B = P_M K_eff on dof blocks, with the pieces of the FP64 pencil."""
+def refined_solve(A, dinv, W, k):
+    """One step of iterative refinement around the k-step semi-iteration:
+    x = P W, e = P (W - A x), result x + e (error operator (I - P A)^2)."""
+    x = cheb_solve(A, dinv, W, k)
+    return x + cheb_solve(A, dinv, W - A @ x, k)
 
-    def __init__(self, sys, k_M, k_P=None):
+
+class Operator:
+    """B = P_M K_eff on dof blocks, with the pieces of the FP64 pencil.
+
+    refine=True applies every inner solve as a refined solve (the inverse
+    the mixed-precision form applies: float semi-iterations around one
+    double residual, here written out in double).
+    """
+
+    def __init__(self, sys, k_M, k_P=None, refine=False):
         self.sys = sys
         self.k_M = k_M
         self.k_P = k_M if k_P is None else k_P
+        self.refine = refine
         self.M = sys.M
         self.dinv_M = 1.0 / sys.M.diagonal()
         self.negAp = -sys.A_p if sys.has_fluid() else None
@@ -86,12 +99,14 @@ class Operator:
         Y = self.sys.A_G @ X
         if self.negAp is not None:
             q = self.sys.E_G.T @ X
-            s = cheb_solve(self.negAp, self.dinv_P, np.asarray(q), self.k_P)
+            solve = refined_solve if self.refine else cheb_solve
+            s = solve(self.negAp, self.dinv_P, np.asarray(q), self.k_P)
             Y = Y + self.sys.E_G @ s
         return np.asarray(Y)
 
     def Minv(self, W):
-        return cheb_solve(self.M, self.dinv_M, W, self.k_M)
+        solve = refined_solve if self.refine else cheb_solve
+        return solve(self.M, self.dinv_M, W, self.k_M)
 
     def B(self, X):
         return self.Minv(self.K(X))
@@ -185,10 +200,16 @@ def lanczos_bounds(op: Operator, n, steps=40, seed=0):
 
 
 def spectrum_bounds(op: Operator, n, steps=40, seed=0):
-    """[l_lo, l_hi] enclosing the spectrum of B: 40-step estimate, margins."""
+    """[l_lo, l_hi] for the Chebyshev map of B: 40-step Lanczos estimate.
+
+    l_hi = 1.01 (theta_max + |residual|) encloses the top. l_lo = min(0,
+    theta_min) - 1e-6 l_hi: the bottom Ritz value without its (large,
+    unconverged) residual; an undershoot delta only lets T_d grow to
+    cosh(d sqrt(2 delta / e)) ~ 1 for delta << e / d^2.
+    """
     th, res = lanczos_bounds(op, n, steps, seed)
     hi = (th[-1] + res[-1]) * 1.01
-    lo = min(0.0, th[0] - res[0]) - 1e-4 * hi
+    lo = min(0.0, th[0]) - 1e-6 * hi
     return lo, hi
 
 

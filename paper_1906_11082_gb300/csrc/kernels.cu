@@ -1,0 +1,548 @@
+// Hot-path sparse kernels for sm_103a.
+//
+// Data layout: a block of b vectors over the displacement dofs is a
+// row-major (n x b) array with a leading dimension; dof 3*i + k of node i
+// lives in row 3*i + k, so one node's 3 x b values are three runs of b
+// consecutive entries. Each node row of a sparse matrix is handled by a
+// group of TPR = min(32, next_pow2(b)) threads; thread `lane` of the group
+// owns the columns lane, lane + TPR (b <= 64) and all components of them.
+// A gather of a neighbour node therefore reads 3 coalesced runs of b
+// values per stored block, and the matrix values and column index are
+// broadcast to the group.
+#include "kernels.h"
+
+#include <atomic>
+#include <cstdio>
+#include <type_traits>
+
+#include "nm_internal.h"
+
+namespace nm {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+static inline int tpr_shift_for(int b) {
+    int t = b < 32 ? b : 32;
+    int s = 0;
+    while ((1 << s) < t) ++s;
+    return s;
+}
+
+constexpr int kThreads = 256;
+
+// ----------------------------------------------------------------- A (x) I_R
+template <typename T, int R, int CPT, int MODE>
+__global__ void __launch_bounds__(kThreads) kron_kernel(const KronArgs<T> a, int tpr_shift) {
+    const int tpr = 1 << tpr_shift;
+    const int lane = threadIdx.x & (tpr - 1);
+    const int64_t row = (int64_t)blockIdx.x * (kThreads >> tpr_shift) + (threadIdx.x >> tpr_shift);
+    if (row >= a.nrows) return;
+    T acc[CPT][R];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q)
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[q][k] = T(0);
+    const int e0 = __ldg(a.rowptr + row), e1 = __ldg(a.rowptr + row + 1);
+    for (int e = e0; e < e1; ++e) {
+        const int64_t j = __ldg(a.col + e);
+        const T v = __ldg(a.val + e);
+        const T* xj = a.X + (int64_t)R * j * a.ldx;
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int c = lane + q * tpr;
+            if (c < a.b) {
+#pragma unroll
+                for (int k = 0; k < R; ++k) acc[q][k] += v * __ldg(xj + k * a.ldx + c);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int c = lane + q * tpr;
+        if (c >= a.b) continue;
+        if (MODE == KRON_PLAIN) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) a.Y[(R * row + k) * a.ldy + c] = acc[q][k];
+        } else if (MODE == KRON_CORI) {
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                T y = T(0);
+#pragma unroll
+                for (int k = 0; k < R; ++k) y += a.sk[m * 3 + k] * acc[q][k];
+                a.Y[(R * row + m) * a.ldy + c] = y;
+            }
+        } else {
+            const T d = a.dinv[row] * a.inv_theta;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const int64_t r = R * row + k;
+                const T xk = a.X[r * a.ldx + c];
+                const T w = a.W[r * a.ldw + c];
+                const T xp = a.Xp ? a.Xp[r * a.ldp + c] : T(0);
+                const T xn = xp + a.om * (xk - xp + d * (w - acc[q][k]));
+                if (MODE == KRON_CHEB) {
+                    a.Xn[r * a.ldn + c] = xn;
+                } else {
+                    const T tk = a.Tk[r * a.ldtk + c];
+                    const T tp = a.Tp ? a.Tp[r * a.ldtp + c] : T(0);
+                    const T tn = a.a1 * (xn - a.cshift * tk) - a.a2 * tp;
+                    a.Tn[r * a.ldtn + c] = tn;
+                    if (a.Z) a.Z[r * a.ldz + c] += a.gam * tn;
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int R, int MODE>
+static int kron_dispatch_cpt(int cpt, const KronArgs<T>& a, int shift, cudaStream_t s) {
+    const int rows_per_block = kThreads >> shift;
+    const int64_t grid = (a.nrows + rows_per_block - 1) / rows_per_block;
+    if (grid == 0) return NM_OK;
+    if (cpt == 1)
+        kron_kernel<T, R, 1, MODE><<<(unsigned)grid, kThreads, 0, s>>>(a, shift);
+    else
+        kron_kernel<T, R, 2, MODE><<<(unsigned)grid, kThreads, 0, s>>>(a, shift);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+template <typename T>
+int launch_kron(int R, int mode, const KronArgs<T>& a, cudaStream_t s) {
+    if (a.b < 1 || a.b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
+    const int shift = tpr_shift_for(a.b);
+    const int cpt = (a.b + (1 << shift) - 1) >> shift;
+    if (R == 3) {
+        switch (mode) {
+            case KRON_PLAIN: return kron_dispatch_cpt<T, 3, KRON_PLAIN>(cpt, a, shift, s);
+            case KRON_CHEB: return kron_dispatch_cpt<T, 3, KRON_CHEB>(cpt, a, shift, s);
+            case KRON_CHEB_FILT: return kron_dispatch_cpt<T, 3, KRON_CHEB_FILT>(cpt, a, shift, s);
+            case KRON_CORI: return kron_dispatch_cpt<T, 3, KRON_CORI>(cpt, a, shift, s);
+        }
+    } else if (R == 1) {
+        switch (mode) {
+            case KRON_PLAIN: return kron_dispatch_cpt<T, 1, KRON_PLAIN>(cpt, a, shift, s);
+            case KRON_CHEB: return kron_dispatch_cpt<T, 1, KRON_CHEB>(cpt, a, shift, s);
+            default: break;
+        }
+    }
+    return fail(NM_EINVAL, "unsupported kron mode");
+}
+
+// ----------------------------------------------------------------- 3x3 BSR
+template <typename T, int CPT>
+__global__ void __launch_bounds__(kThreads) bsr33_kernel(const Bsr33Args<T> a, int tpr_shift) {
+    const int tpr = 1 << tpr_shift;
+    const int lane = threadIdx.x & (tpr - 1);
+    const int64_t row = (int64_t)blockIdx.x * (kThreads >> tpr_shift) + (threadIdx.x >> tpr_shift);
+    if (row >= a.nrows) return;
+    T acc[CPT][3];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) acc[q][0] = acc[q][1] = acc[q][2] = T(0);
+    const int e0 = __ldg(a.rowptr + row), e1 = __ldg(a.rowptr + row + 1);
+    for (int e = e0; e < e1; ++e) {
+        const int64_t j = __ldg(a.col + e);
+        const T* K = a.val + 9 * (int64_t)e;
+        T k[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) k[t] = __ldg(K + t);
+        const T* xj = a.X + 3 * j * a.ldx;
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int c = lane + q * tpr;
+            if (c < a.b) {
+                const T x0 = __ldg(xj + c), x1 = __ldg(xj + a.ldx + c), x2 = __ldg(xj + 2 * a.ldx + c);
+                acc[q][0] += k[0] * x0 + k[1] * x1 + k[2] * x2;
+                acc[q][1] += k[3] * x0 + k[4] * x1 + k[5] * x2;
+                acc[q][2] += k[6] * x0 + k[7] * x1 + k[8] * x2;
+            }
+        }
+    }
+    if (a.e_rowptr) {
+        const int f0 = __ldg(a.e_rowptr + row), f1 = __ldg(a.e_rowptr + row + 1);
+        for (int e = f0; e < f1; ++e) {
+            const int64_t p = __ldg(a.e_col + e);
+            const T v0 = __ldg(a.e_val + 3 * (int64_t)e), v1 = __ldg(a.e_val + 3 * (int64_t)e + 1),
+                    v2 = __ldg(a.e_val + 3 * (int64_t)e + 2);
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                const int c = lane + q * tpr;
+                if (c < a.b) {
+                    const T sv = __ldg(a.S + p * a.lds + c);
+                    acc[q][0] += v0 * sv;
+                    acc[q][1] += v1 * sv;
+                    acc[q][2] += v2 * sv;
+                }
+            }
+        }
+    }
+    const T d = a.X1 ? a.dinv[row] * a.inv_theta : T(0);
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int c = lane + q * tpr;
+        if (c >= a.b) continue;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            a.W[(3 * row + m) * a.ldw + c] = acc[q][m];
+            if (a.X1) a.X1[(3 * row + m) * a.ldx1 + c] = d * acc[q][m];
+        }
+    }
+}
+
+template <typename T>
+int launch_bsr33(const Bsr33Args<T>& a, cudaStream_t s) {
+    if (a.b < 1 || a.b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
+    const int shift = tpr_shift_for(a.b);
+    const int cpt = (a.b + (1 << shift) - 1) >> shift;
+    const int rows_per_block = kThreads >> shift;
+    const int64_t grid = (a.nrows + rows_per_block - 1) / rows_per_block;
+    if (grid == 0) return NM_OK;
+    if (cpt == 1)
+        bsr33_kernel<T, 1><<<(unsigned)grid, kThreads, 0, s>>>(a, shift);
+    else
+        bsr33_kernel<T, 2><<<(unsigned)grid, kThreads, 0, s>>>(a, shift);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+// ----------------------------------------------------------------- 1x3 BSR
+template <typename T, int CPT>
+__global__ void __launch_bounds__(kThreads) bsr13_kernel(const Bsr13Args<T> a, int tpr_shift) {
+    const int tpr = 1 << tpr_shift;
+    const int lane = threadIdx.x & (tpr - 1);
+    const int64_t row = (int64_t)blockIdx.x * (kThreads >> tpr_shift) + (threadIdx.x >> tpr_shift);
+    if (row >= a.nrows) return;
+    T acc[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) acc[q] = T(0);
+    const int e0 = __ldg(a.rowptr + row), e1 = __ldg(a.rowptr + row + 1);
+    for (int e = e0; e < e1; ++e) {
+        const int64_t j = __ldg(a.col + e);
+        const T v0 = __ldg(a.val + 3 * (int64_t)e), v1 = __ldg(a.val + 3 * (int64_t)e + 1),
+                v2 = __ldg(a.val + 3 * (int64_t)e + 2);
+        const T* xj = a.X + 3 * j * a.ldx;
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int c = lane + q * tpr;
+            if (c < a.b)
+                acc[q] += v0 * __ldg(xj + c) + v1 * __ldg(xj + a.ldx + c) + v2 * __ldg(xj + 2 * a.ldx + c);
+        }
+    }
+    const T d = a.S1 ? a.dinv[row] * a.inv_theta : T(0);
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int c = lane + q * tpr;
+        if (c >= a.b) continue;
+        a.Q[row * a.ldq + c] = acc[q];
+        if (a.S1) a.S1[row * a.lds1 + c] = d * acc[q];
+    }
+}
+
+template <typename T>
+int launch_bsr13(const Bsr13Args<T>& a, cudaStream_t s) {
+    if (a.b < 1 || a.b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
+    const int shift = tpr_shift_for(a.b);
+    const int cpt = (a.b + (1 << shift) - 1) >> shift;
+    const int rows_per_block = kThreads >> shift;
+    const int64_t grid = (a.nrows + rows_per_block - 1) / rows_per_block;
+    if (grid == 0) return NM_OK;
+    if (cpt == 1)
+        bsr13_kernel<T, 1><<<(unsigned)grid, kThreads, 0, s>>>(a, shift);
+    else
+        bsr13_kernel<T, 2><<<(unsigned)grid, kThreads, 0, s>>>(a, shift);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+// ----------------------------------------------------------------- small kernels
+template <typename T>
+__global__ void scale_copy_kernel(int64_t rows, int b, T alpha, const T* X, int64_t ldx, T* Y,
+                                  int64_t ldy) {
+    const int64_t total = rows * b;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / b;
+        const int c = (int)(t - i * b);
+        Y[i * ldy + c] = alpha * X[i * ldx + c];
+    }
+}
+
+static unsigned grid_for(int64_t total) {
+    int64_t g = (total + kThreads - 1) / kThreads;
+    if (g > 152 * 32) g = 152 * 32;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+template <typename T>
+int launch_scale_copy(int64_t rows, int b, T alpha, const T* X, int64_t ldx, T* Y, int64_t ldy,
+                      cudaStream_t s) {
+    if (rows * b == 0) return NM_OK;
+    scale_copy_kernel<T><<<grid_for(rows * b), kThreads, 0, s>>>(rows, b, alpha, X, ldx, Y, ldy);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+template <typename Tin, typename Tout>
+__global__ void convert_kernel(int64_t rows, int b, const Tin* X, int64_t ldx, Tout* Y, int64_t ldy) {
+    const int64_t total = rows * b;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / b;
+        const int c = (int)(t - i * b);
+        Y[i * ldy + c] = (Tout)X[i * ldx + c];
+    }
+}
+
+template <typename Tin, typename Tout>
+int launch_convert(int64_t rows, int b, const Tin* X, int64_t ldx, Tout* Y, int64_t ldy,
+                   cudaStream_t s) {
+    if (rows * b == 0) return NM_OK;
+    convert_kernel<Tin, Tout><<<grid_for(rows * b), kThreads, 0, s>>>(rows, b, X, ldx, Y, ldy);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+__global__ void d2f_kernel(int64_t n, const double* x, float* y) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x)
+        y[t] = (float)x[t];
+}
+
+int launch_d2f(int64_t n, const double* x, float* y, cudaStream_t s) {
+    if (n == 0) return NM_OK;
+    d2f_kernel<<<grid_for(n), kThreads, 0, s>>>(n, x, y);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+// column sums of squares: threadIdx.x over 32 columns, blocks stride over rows
+__global__ void colnorm2_kernel(int64_t rows, int b, const double* X, int64_t ldx, double* out) {
+    const int c = blockIdx.y * 32 + threadIdx.x;
+    double s = 0.0;
+    if (c < b) {
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.y + threadIdx.y; i < rows;
+             i += (int64_t)gridDim.x * blockDim.y) {
+            const double v = X[i * ldx + c];
+            s += v * v;
+        }
+    }
+    __shared__ double red[8][33];
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < b) {
+        double t = 0.0;
+        for (int y = 0; y < (int)blockDim.y; ++y) t += red[y][threadIdx.x];
+        atomicAdd(out + c, t);
+    }
+}
+
+int launch_colnorm2(int64_t rows, int b, const double* X, int64_t ldx, double* out, cudaStream_t s) {
+    if (rows == 0 || b == 0) return NM_OK;
+    dim3 block(32, 8);
+    int64_t gx = (rows + 8 * 64 - 1) / (8 * 64);
+    if (gx > 152 * 4) gx = 152 * 4;
+    dim3 grid((unsigned)gx, (unsigned)((b + 31) / 32));
+    colnorm2_kernel<<<grid, block, 0, s>>>(rows, b, X, ldx, out);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+__global__ void resid_block_kernel(int64_t rows, int b, const double* KX, const double* MX,
+                                   const double* lam, double* R) {
+    const int64_t total = rows * b;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t % b);
+        R[t] = KX[t] - lam[c] * MX[t];
+    }
+}
+
+int launch_resid_block(int64_t rows, int b, const double* KX, const double* MX, const double* lam,
+                       double* R, cudaStream_t s) {
+    if (rows * b == 0) return NM_OK;
+    resid_block_kernel<<<grid_for(rows * b), kThreads, 0, s>>>(rows, b, KX, MX, lam, R);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+template <typename T>
+__global__ void dscale_kernel(int R, int64_t nodes, int b, T inv_theta, const T* dinv, const T* W, int64_t ldw,
+                              T* X, int64_t ldx) {
+    const int64_t total = (int64_t)R * nodes * b;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / b;
+        const int c = (int)(t - r * b);
+        X[r * ldx + c] = inv_theta * dinv[r / R] * W[r * ldw + c];
+    }
+}
+
+template <typename T>
+int launch_dscale(int R, int64_t nodes, int b, T inv_theta, const T* dinv, const T* W, int64_t ldw, T* X,
+                  int64_t ldx, cudaStream_t s) {
+    const int64_t total = (int64_t)R * nodes * b;
+    if (total == 0) return NM_OK;
+    dscale_kernel<T><<<grid_for(total), kThreads, 0, s>>>(R, nodes, b, inv_theta, dinv, W, ldw, X, ldx);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+template <int R, int CPT>
+__global__ void __launch_bounds__(kThreads) resid_mixed_kernel(int64_t nodes, const int* __restrict__ rowptr,
+                                                               const int* __restrict__ col,
+                                                               const double* __restrict__ val,
+                                                               const double* __restrict__ W, int64_t ldw,
+                                                               const float* __restrict__ x, float* r, int b,
+                                                               int tpr_shift) {
+    const int tpr = 1 << tpr_shift;
+    const int lane = threadIdx.x & (tpr - 1);
+    const int64_t row = (int64_t)blockIdx.x * (kThreads >> tpr_shift) + (threadIdx.x >> tpr_shift);
+    if (row >= nodes) return;
+    double acc[CPT][R];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q)
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[q][k] = 0.0;
+    const int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
+    for (int e = e0; e < e1; ++e) {
+        const int64_t j = __ldg(col + e);
+        const double v = __ldg(val + e);
+        const float* xj = x + (int64_t)R * j * b;
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int c = lane + q * tpr;
+            if (c < b) {
+#pragma unroll
+                for (int k = 0; k < R; ++k) acc[q][k] += v * (double)__ldg(xj + k * b + c);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int c = lane + q * tpr;
+        if (c >= b) continue;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int64_t rr = R * row + k;
+            r[rr * b + c] = (float)(W[rr * ldw + c] - acc[q][k]);
+        }
+    }
+}
+
+int launch_resid_mixed(int R, int64_t nodes, const int* rowptr, const int* col, const double* val,
+                       const double* W, int64_t ldw, const float* x32, float* r32, int b, cudaStream_t s) {
+    if (b < 1 || b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
+    const int shift = tpr_shift_for(b);
+    const int cpt = (b + (1 << shift) - 1) >> shift;
+    const int64_t grid = (nodes + (kThreads >> shift) - 1) / (kThreads >> shift);
+    if (grid == 0) return NM_OK;
+    if (R == 3 && cpt == 1)
+        resid_mixed_kernel<3, 1><<<(unsigned)grid, kThreads, 0, s>>>(nodes, rowptr, col, val, W, ldw, x32, r32, b, shift);
+    else if (R == 3)
+        resid_mixed_kernel<3, 2><<<(unsigned)grid, kThreads, 0, s>>>(nodes, rowptr, col, val, W, ldw, x32, r32, b, shift);
+    else if (cpt == 1)
+        resid_mixed_kernel<1, 1><<<(unsigned)grid, kThreads, 0, s>>>(nodes, rowptr, col, val, W, ldw, x32, r32, b, shift);
+    else
+        resid_mixed_kernel<1, 2><<<(unsigned)grid, kThreads, 0, s>>>(nodes, rowptr, col, val, W, ldw, x32, r32, b, shift);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+__global__ void combine_kernel(const CombineArgs a) {
+    const int64_t total = a.rows * a.b;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double sv = (double)a.x32[t] + (double)a.e32[t];
+        if (!a.Tn) {
+            a.out[t] = sv;
+            continue;
+        }
+        const double tp = a.Tp ? a.Tp[t] : 0.0;
+        const double tn = a.a1 * (sv - a.cshift * a.Tk[t]) - a.a2 * tp;
+        a.Tn[t] = tn;
+        if (a.Z) {
+            const int64_t i = t / a.b;
+            const int c = (int)(t - i * a.b);
+            a.Z[i * a.ldz + c] += a.gam * tn;
+        }
+    }
+}
+
+int launch_combine(const CombineArgs& a, cudaStream_t s) {
+    if (a.rows * a.b == 0) return NM_OK;
+    combine_kernel<<<grid_for(a.rows * a.b), kThreads, 0, s>>>(a);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two
+// 32x32->64 multiplies with the published multipliers and Weyl key bumps.
+__device__ inline void philox_round(uint32_t c[4], uint32_t k[2]) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k[0];
+    const uint32_t n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+__global__ void philox_normal_kernel(int64_t count, uint64_t seed, double* out) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; 2 * t < count;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c[4] = {(uint32_t)t, (uint32_t)(t >> 32), 0u, 0u};
+        uint32_t k[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        for (int r = 0; r < 10; ++r) {
+            philox_round(c, k);
+            k[0] += 0x9E3779B9u;
+            k[1] += 0xBB67AE85u;
+        }
+        // two uniforms in (0, 1) with 53-bit resolution, then Box-Muller
+        const double u1 = ((double)(((uint64_t)c[0] << 21) ^ c[1]) + 0.5) * 0x1p-53;
+        const double u2 = ((double)(((uint64_t)c[2] << 21) ^ c[3]) + 0.5) * 0x1p-53;
+        const double r = sqrt(-2.0 * log(u1));
+        const double th = 6.283185307179586 * u2;
+        out[2 * t] = r * cos(th);
+        if (2 * t + 1 < count) out[2 * t + 1] = r * sin(th);
+    }
+}
+
+int launch_philox_normal(int64_t count, uint64_t seed, double* out, cudaStream_t s) {
+    if (count == 0) return NM_OK;
+    philox_normal_kernel<<<grid_for((count + 1) / 2), kThreads, 0, s>>>(count, seed, out);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+template int launch_kron<double>(int, int, const KronArgs<double>&, cudaStream_t);
+template int launch_kron<float>(int, int, const KronArgs<float>&, cudaStream_t);
+template int launch_bsr33<double>(const Bsr33Args<double>&, cudaStream_t);
+template int launch_bsr33<float>(const Bsr33Args<float>&, cudaStream_t);
+template int launch_bsr13<double>(const Bsr13Args<double>&, cudaStream_t);
+template int launch_bsr13<float>(const Bsr13Args<float>&, cudaStream_t);
+template int launch_dscale<double>(int, int64_t, int, double, const double*, const double*, int64_t, double*, int64_t, cudaStream_t);
+template int launch_dscale<float>(int, int64_t, int, float, const float*, const float*, int64_t, float*, int64_t, cudaStream_t);
+template int launch_scale_copy<double>(int64_t, int, double, const double*, int64_t, double*, int64_t, cudaStream_t);
+template int launch_scale_copy<float>(int64_t, int, float, const float*, int64_t, float*, int64_t, cudaStream_t);
+template int launch_convert<double, float>(int64_t, int, const double*, int64_t, float*, int64_t, cudaStream_t);
+template int launch_convert<float, double>(int64_t, int, const float*, int64_t, double*, int64_t, cudaStream_t);
+
+}  // namespace nm

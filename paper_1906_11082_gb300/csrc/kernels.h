@@ -1,0 +1,131 @@
+// Launchers of the hot-path sparse kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace nm {
+
+// Process-wide count of kernels launched by the library (nm_kernel_launches).
+void count_launch(uint64_t n = 1);
+
+enum KronMode { KRON_PLAIN = 0, KRON_CHEB = 1, KRON_CHEB_FILT = 2, KRON_CORI = 3 };
+
+// Y (or the Chebyshev / filter epilogue) from the scalar CSR matrix A
+// applied as A (x) I_R to row-major blocks of b columns. A node row i owns
+// the R consecutive rows R*i .. R*i+R-1 of every block.
+template <typename T>
+struct KronArgs {
+    int nrows = 0;
+    const int* rowptr = nullptr;
+    const int* col = nullptr;
+    const T* val = nullptr;
+    const T* dinv = nullptr;
+    int b = 0;
+    const T* X = nullptr;   int64_t ldx = 0;   // gathered operand x_k
+    T* Y = nullptr;         int64_t ldy = 0;   // PLAIN / CORI output
+    const T* W = nullptr;   int64_t ldw = 0;   // CHEB right-hand side
+    const T* Xp = nullptr;  int64_t ldp = 0;   // CHEB x_{k-1} (nullptr: zero)
+    T* Xn = nullptr;        int64_t ldn = 0;   // CHEB x_{k+1} (may alias Xp)
+    T om = 0, inv_theta = 0;
+    const T* Tk = nullptr;  int64_t ldtk = 0;  // FILT current Chebyshev block
+    const T* Tp = nullptr;  int64_t ldtp = 0;  // FILT previous (nullptr: zero)
+    T* Tn = nullptr;        int64_t ldtn = 0;  // FILT next (may alias Tp)
+    T* Z = nullptr;         int64_t ldz = 0;   // FILT accumulator (nullptr: none)
+    T a1 = 0, cshift = 0, a2 = 0, gam = 0;
+    T sk[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};      // CORI 3x3 (row-major)
+};
+
+template <typename T>
+int launch_kron(int R, int mode, const KronArgs<T>& a, cudaStream_t s);
+
+// W = A X (+ E S) for the 3x3-block CSR A over u-nodes and the optional
+// 3x1-block CSR E (u-nodes x p-nodes) applied to the pressure block S.
+// With X1 != nullptr also writes the first semi-iterate X1 = inv_theta *
+// dinv[i] * W of the mass solve.
+template <typename T>
+struct Bsr33Args {
+    int nrows = 0;
+    const int* rowptr = nullptr;
+    const int* col = nullptr;
+    const T* val = nullptr;
+    const int* e_rowptr = nullptr;
+    const int* e_col = nullptr;
+    const T* e_val = nullptr;
+    const T* S = nullptr;   int64_t lds = 0;
+    int b = 0;
+    const T* X = nullptr;   int64_t ldx = 0;
+    T* W = nullptr;         int64_t ldw = 0;
+    T* X1 = nullptr;        int64_t ldx1 = 0;
+    const T* dinv = nullptr;
+    T inv_theta = 0;
+};
+
+template <typename T>
+int launch_bsr33(const Bsr33Args<T>& a, cudaStream_t s);
+
+// Q = E^T X for the 1x3-block CSR E^T (p-nodes x u-nodes); with S1 !=
+// nullptr also S1 = inv_theta * dinv[p] * Q.
+template <typename T>
+struct Bsr13Args {
+    int nrows = 0;
+    const int* rowptr = nullptr;
+    const int* col = nullptr;
+    const T* val = nullptr;
+    int b = 0;
+    const T* X = nullptr;   int64_t ldx = 0;
+    T* Q = nullptr;         int64_t ldq = 0;
+    T* S1 = nullptr;        int64_t lds1 = 0;
+    const T* dinv = nullptr;
+    T inv_theta = 0;
+};
+
+template <typename T>
+int launch_bsr13(const Bsr13Args<T>& a, cudaStream_t s);
+
+// X[(R i + k), c] = inv_theta * dinv[i] * W[(R i + k), c] (first semi-iterate).
+template <typename T>
+int launch_dscale(int R, int64_t nodes, int b, T inv_theta, const T* dinv, const T* W, int64_t ldw, T* X,
+                  int64_t ldx, cudaStream_t s);
+
+// r32 = float(W - (A (x) I_R) x32) with double matrix values and double
+// sums over the float iterate (the refinement residual of a mixed solve).
+int launch_resid_mixed(int R, int64_t nodes, const int* rowptr, const int* col, const double* val,
+                       const double* W, int64_t ldw, const float* x32, float* r32, int b, cudaStream_t s);
+
+// S = double(x32) + double(e32); with Tn != nullptr the outer filter update
+// Tn = a1 (S - c Tk) - a2 Tp, Z += gam Tn, else out = S.
+struct CombineArgs {
+    int64_t rows = 0;
+    int b = 0;
+    const float* x32 = nullptr;
+    const float* e32 = nullptr;
+    double* out = nullptr;
+    const double* Tk = nullptr;
+    const double* Tp = nullptr;
+    double* Tn = nullptr;
+    double* Z = nullptr;
+    int64_t ldz = 0;
+    double a1 = 0, cshift = 0, a2 = 0, gam = 0;
+};
+int launch_combine(const CombineArgs& a, cudaStream_t s);
+
+// Y[i, c] = alpha * X[i, c] (rows x b, row-major with leading dims).
+template <typename T>
+int launch_scale_copy(int64_t rows, int b, T alpha, const T* X, int64_t ldx, T* Y, int64_t ldy,
+                      cudaStream_t s);
+// Y[i, c] = X[i, c] converted between float and double.
+template <typename Tin, typename Tout>
+int launch_convert(int64_t rows, int b, const Tin* X, int64_t ldx, Tout* Y, int64_t ldy,
+                   cudaStream_t s);
+int launch_d2f(int64_t n, const double* x, float* y, cudaStream_t s);
+// out[c] += sum_i X[i, c]^2 (out zeroed by the caller).
+int launch_colnorm2(int64_t rows, int b, const double* X, int64_t ldx, double* out,
+                    cudaStream_t s);
+// R[i, c] = KX[i, c] - lam[c] * MX[i, c]
+int launch_resid_block(int64_t rows, int b, const double* KX, const double* MX,
+                       const double* lam, double* R, cudaStream_t s);
+// Philox-4x32-10 Gaussian block (Box-Muller), counter = element index.
+int launch_philox_normal(int64_t count, uint64_t seed, double* out, cudaStream_t s);
+
+}  // namespace nm

@@ -1,0 +1,138 @@
+// Internal structures of the nm library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/nm.h"
+
+namespace nm {
+
+// Error propagation inside the library: every failing call sets the
+// context message and returns a code; nothing throws across the ABI.
+struct Status {
+    int code = NM_OK;
+    std::string msg;
+};
+
+#define NM_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return ::nm::fail(NM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define NM_CUBLAS(call)                                                                    \
+    do {                                                                                   \
+        cublasStatus_t s_ = (call);                                                        \
+        if (s_ != CUBLAS_STATUS_SUCCESS)                                                   \
+            return ::nm::fail(NM_ECUDA, std::string(#call) + ": cublas status " +           \
+                                            std::to_string((int)s_));                      \
+    } while (0)
+
+#define NM_CUSOLVER(call)                                                                  \
+    do {                                                                                   \
+        cusolverStatus_t s_ = (call);                                                      \
+        if (s_ != CUSOLVER_STATUS_SUCCESS)                                                 \
+            return ::nm::fail(NM_ECUDA, std::string(#call) + ": cusolver status " +         \
+                                            std::to_string((int)s_));                      \
+    } while (0)
+
+#define NM_TRY(expr)                 \
+    do {                             \
+        int r_ = (expr);             \
+        if (r_ != NM_OK) return r_;  \
+    } while (0)
+
+int fail(int code, const std::string& msg);   // records msg for nm_last_error
+void set_thread_ctx(nm_ctx* ctx);
+
+// Device buffer owned by the library.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    int alloc(size_t nbytes);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(p); }
+    ~DevBuf() { release(); }
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+};
+
+// Sparse matrices on the device. Block CSR with rb x cb blocks, values
+// row-major inside a block, stored in double and (lazily) in float.
+struct DevCSR {
+    int64_t nrows = 0, ncols = 0, nnz = 0;
+    int rb = 1, cb = 1;
+    DevBuf rowptr;   // int32 [nrows + 1]  (nnz < 2^31 checked at build)
+    DevBuf col;      // int32 [nnz]
+    DevBuf val;      // double [nnz * rb * cb]
+    DevBuf val32;    // float  [nnz * rb * cb] (on demand)
+    DevBuf dinv;     // inverse diagonal (scalar square matrices only), double
+    DevBuf dinv32;
+    std::vector<int32_t> h_rowptr, h_col;   // host copy of the pattern
+};
+
+struct Workspace {
+    DevBuf buf;      // filter recurrence scratch
+    size_t bytes = 0;
+};
+
+}  // namespace nm
+
+struct nm_ctx {
+    int device = 0;
+    std::string last_error;
+    cublasHandle_t cublas = nullptr;
+    cusolverDnHandle_t cusolver = nullptr;
+    cudaStream_t stream = nullptr;   // library-owned stream for blocking calls
+};
+
+struct nm_problem {
+    nm_ctx* ctx = nullptr;
+    nm_problem_info info{};
+    // maps (host)
+    std::vector<int64_t> canon_of_internal;   // [Nu]
+    std::vector<int64_t> p2_of_internal;      // [Nu]
+    std::vector<int64_t> pcanon_of_internal;  // [Np]
+    // device matrices
+    nm::DevCSR AG;     // 3x3 blocks, u x u
+    nm::DevCSR Mr;     // scalar, u x u (same pattern as AG)
+    nm::DevCSR Pn;     // scalar -A_p, p x p
+    nm::DevCSR EG;     // 3x1 blocks, u x p
+    nm::DevCSR EGt;    // 1x3 blocks, p x u
+    nm::DevBuf g;      // double [Nu * 3] reference field at u-nodes
+    double Omega[3] = {0, 0, 0};
+    uint32_t flags = 0;
+    // slice
+    double lo = 0, hi = 0;
+    int have_interval = 0;
+    double bounds_lo = 0, bounds_hi = 0;
+    int have_bounds = 0;
+    // kernel timing (nm_profile): event pairs per region kind
+    int profile = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_regions;  // kind, (start, stop)
+    std::vector<int64_t> ev_launches;   // launches inside each region
+    size_t ev_next = 0;
+    // scratch for the filter recurrence
+    nm::Workspace ws;
+    nm::DevBuf pscratch;     // pressure-sized scratch for the Schur term
+};
+
+namespace nm {
+// Begin / end a timed launch region on stream s (no-ops unless profiling).
+int prof_begin(nm_problem* P, cudaStream_t s, cudaEvent_t* start);
+int prof_end(nm_problem* P, cudaStream_t s, int kind, cudaEvent_t start, int64_t launches);
+}  // namespace nm
+
+struct nm_result {
+    nm_result_info info{};
+    std::vector<double> lambda, resid;
+    nm::DevBuf X;
+};

@@ -1,0 +1,1261 @@
+// Filter recurrence, operator pieces, spectrum bounds, filtered block
+// Lanczos, Rayleigh-Ritz and the rotating projection (paper Sec. 6.2, 7).
+//
+// All vectors stay on the device; the host only sequences launches and
+// reads small results (Ritz values, residual norms) at convergence tests.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <memory>
+#include <cstring>
+#include <vector>
+
+#include "kernels.h"
+#include "nm_internal.h"
+
+namespace nm {
+
+int ensure_f32(nm_problem* P, cudaStream_t s);
+
+static const double kMassLo = 0.25;
+static const double kMassHi = (19.0 + 15.779733838059499) / 8.0;   // (19 + sqrt(249)) / 8
+
+template <typename T>
+struct Mats {
+    int64_t Nu = 0, Np = 0;
+    const int *u_rp = nullptr, *u_col = nullptr;
+    const T *AG = nullptr, *Mr = nullptr, *dM = nullptr;
+    const int *p_rp = nullptr, *p_col = nullptr;
+    const T *Pn = nullptr, *dP = nullptr;
+    const int *e_rp = nullptr, *e_col = nullptr;
+    const T* EG = nullptr;
+    const int *et_rp = nullptr, *et_col = nullptr;
+    const T* EGt = nullptr;
+};
+
+template <typename T>
+static const T* vals(const DevCSR& A);
+template <>
+const double* vals<double>(const DevCSR& A) { return A.val.as<double>(); }
+template <>
+const float* vals<float>(const DevCSR& A) { return A.val32.as<float>(); }
+template <typename T>
+static const T* dinv(const DevCSR& A);
+template <>
+const double* dinv<double>(const DevCSR& A) { return A.dinv.as<double>(); }
+template <>
+const float* dinv<float>(const DevCSR& A) { return A.dinv32.as<float>(); }
+
+template <typename T>
+static Mats<T> mats(nm_problem* P) {
+    Mats<T> m;
+    m.Nu = P->info.Nu;
+    m.Np = P->info.Np;
+    m.u_rp = P->AG.rowptr.as<int>();
+    m.u_col = P->AG.col.as<int>();
+    m.AG = vals<T>(P->AG);
+    m.Mr = vals<T>(P->Mr);
+    m.dM = dinv<T>(P->Mr);
+    if (m.Np > 0) {
+        m.p_rp = P->Pn.rowptr.as<int>();
+        m.p_col = P->Pn.col.as<int>();
+        m.Pn = vals<T>(P->Pn);
+        m.dP = dinv<T>(P->Pn);
+        m.e_rp = P->EG.rowptr.as<int>();
+        m.e_col = P->EG.col.as<int>();
+        m.EG = vals<T>(P->EG);
+        m.et_rp = P->EGt.rowptr.as<int>();
+        m.et_col = P->EGt.col.as<int>();
+        m.EGt = vals<T>(P->EGt);
+    }
+    return m;
+}
+
+struct ChebCoef {
+    double inv_theta, four_sig2;
+    ChebCoef(double lo, double hi) {
+        const double th = 0.5 * (hi + lo), de = 0.5 * (hi - lo);
+        inv_theta = 1.0 / th;
+        four_sig2 = 4.0 * (th / de) * (th / de);
+    }
+};
+
+// Scratch for one operator application on b columns.
+template <typename T>
+struct Scratch {
+    T *TA, *TB, *W, *XA, *XB;    // n x b each (ld b)
+    T *Q, *PA, *PB;              // Np x b each
+};
+
+template <typename T>
+static int get_scratch(nm_problem* P, int b, Scratch<T>& S) {
+    const int64_t n = P->info.n, Np = P->info.Np;
+    const size_t need = (size_t)(5 * n + 3 * Np) * b * sizeof(T);
+    if (P->ws.bytes < need) {
+        P->ws.buf.release();
+        NM_TRY(P->ws.buf.alloc(need));
+        P->ws.bytes = need;
+    }
+    T* p = P->ws.buf.as<T>();
+    S.TA = p; p += n * b;
+    S.TB = p; p += n * b;
+    S.W = p; p += n * b;
+    S.XA = p; p += n * b;
+    S.XB = p; p += n * b;
+    S.Q = p; p += Np * b;
+    S.PA = p; p += Np * b;
+    S.PB = p;
+    return NM_OK;
+}
+
+// Pressure Schur solve: returns the buffer holding S ~ (-A_p)^{-1} E_G^T X.
+template <typename T>
+static int schur_pressure(const Mats<T>& m, const T* X, int64_t ldx, int b, int k_P, double lo,
+                          double hi, const Scratch<T>& S, const T** out, cudaStream_t s) {
+    ChebCoef cc(lo, hi);
+    Bsr13Args<T> q;
+    q.nrows = (int)m.Np;
+    q.rowptr = m.et_rp;
+    q.col = m.et_col;
+    q.val = m.EGt;
+    q.b = b;
+    q.X = X;
+    q.ldx = ldx;
+    q.Q = S.Q;
+    q.ldq = b;
+    q.S1 = S.PA;
+    q.lds1 = b;
+    q.dinv = m.dP;
+    q.inv_theta = (T)cc.inv_theta;
+    NM_TRY(launch_bsr13<T>(q, s));
+    T* buf[2] = {S.PB, S.PA};   // buf[1] holds x_1
+    double om = 2.0;
+    for (int j = 2; j <= k_P; ++j) {
+        om = 1.0 / (1.0 - om / cc.four_sig2);
+        KronArgs<T> a;
+        a.nrows = (int)m.Np;
+        a.rowptr = m.p_rp;
+        a.col = m.p_col;
+        a.val = m.Pn;
+        a.dinv = m.dP;
+        a.b = b;
+        a.X = buf[(j - 1) & 1];
+        a.ldx = b;
+        a.W = S.Q;
+        a.ldw = b;
+        a.Xp = j == 2 ? nullptr : buf[j & 1];
+        a.ldp = b;
+        a.Xn = buf[j & 1];
+        a.ldn = b;
+        a.om = (T)om;
+        a.inv_theta = (T)cc.inv_theta;
+        NM_TRY(launch_kron<T>(1, KRON_CHEB, a, s));
+    }
+    *out = buf[k_P & 1];
+    return NM_OK;
+}
+
+// W = K_eff X (optionally X1 = inv_theta D^-1 W for the mass solve).
+template <typename T>
+static int apply_K_t(nm_problem* P, const T* X, int64_t ldx, T* W, int64_t ldw, int b, int k_P,
+                     const Scratch<T>& S, T* X1, double inv_theta_M, cudaStream_t s) {
+    Mats<T> m = mats<T>(P);
+    Bsr33Args<T> a;
+    a.nrows = (int)m.Nu;
+    a.rowptr = m.u_rp;
+    a.col = m.u_col;
+    a.val = m.AG;
+    a.b = b;
+    a.X = X;
+    a.ldx = ldx;
+    a.W = W;
+    a.ldw = ldw;
+    a.X1 = X1;
+    a.ldx1 = b;
+    a.dinv = m.dM;
+    a.inv_theta = (T)inv_theta_M;
+    if (m.Np > 0) {
+        const T* Sp = nullptr;
+        NM_TRY(schur_pressure<T>(m, X, ldx, b, k_P, kMassLo, kMassHi, S, &Sp, s));
+        a.e_rowptr = m.e_rp;
+        a.e_col = m.e_col;
+        a.e_val = m.EG;
+        a.S = Sp;
+        a.lds = b;
+    }
+    return launch_bsr33<T>(a, s);
+}
+
+// Mass-solve semi-iteration steps 2..k_M starting from x_1 in S.XA and the
+// right-hand side S.W. With filt != nullptr the last step is fused with
+// the outer Chebyshev update; otherwise x_{k_M} is copied to Xout.
+struct FiltStep {
+    double a1, cshift, a2, gam;
+};
+
+template <typename T>
+static int mass_steps(const Mats<T>& m, int b, int k_M, double lo, double hi, const Scratch<T>& S,
+                      const FiltStep* filt, const T* Tk, const T* Tp, T* Tn, T* Z, int64_t ldz,
+                      T* Xout, int64_t ldo, cudaStream_t s) {
+    ChebCoef cc(lo, hi);
+    T* buf[2] = {S.XB, S.XA};
+    double om = 2.0;
+    for (int j = 2; j <= k_M; ++j) {
+        om = 1.0 / (1.0 - om / cc.four_sig2);
+        KronArgs<T> a;
+        a.nrows = (int)m.Nu;
+        a.rowptr = m.u_rp;
+        a.col = m.u_col;
+        a.val = m.Mr;
+        a.dinv = m.dM;
+        a.b = b;
+        a.X = buf[(j - 1) & 1];
+        a.ldx = b;
+        a.W = S.W;
+        a.ldw = b;
+        a.Xp = j == 2 ? nullptr : buf[j & 1];
+        a.ldp = b;
+        a.om = (T)om;
+        a.inv_theta = (T)cc.inv_theta;
+        if (j == k_M && filt) {
+            a.Tk = Tk;
+            a.ldtk = b;
+            a.Tp = Tp;
+            a.ldtp = b;
+            a.Tn = Tn;
+            a.ldtn = b;
+            a.Z = Z;
+            a.ldz = ldz;
+            a.a1 = (T)filt->a1;
+            a.cshift = (T)filt->cshift;
+            a.a2 = (T)filt->a2;
+            a.gam = (T)filt->gam;
+            NM_TRY(launch_kron<T>(3, KRON_CHEB_FILT, a, s));
+        } else if (j == k_M && Xout) {
+            a.Xn = Xout;
+            a.ldn = ldo;
+            NM_TRY(launch_kron<T>(3, KRON_CHEB, a, s));
+        } else {
+            a.Xn = buf[j & 1];
+            a.ldn = b;
+            NM_TRY(launch_kron<T>(3, KRON_CHEB, a, s));
+        }
+    }
+    return NM_OK;
+}
+
+template <typename T>
+int filter_apply_t(nm_problem* P, const nm_filter* f, const T* Y, int64_t ldy, T* Z, int64_t ldz,
+                   int b, cudaStream_t s) {
+    const int d = f->degree;
+    if (d < 0 || !f->gamma) return fail(NM_EINVAL, "filter needs degree >= 0 and gamma");
+    if (f->k_M < 2 || (P->info.Np > 0 && f->k_P < 2)) return fail(NM_EINVAL, "k_M and k_P must be >= 2");
+    if (!(f->e > 0)) return fail(NM_EINVAL, "filter half-width e must be positive");
+    const double mlo = f->m_lo > 0 ? f->m_lo : kMassLo;
+    const double mhi = f->m_hi > 0 ? f->m_hi : kMassHi;
+    if (!(mhi > mlo)) return fail(NM_EINVAL, "mass bounds need m_hi > m_lo > 0");
+    const int64_t n = P->info.n;
+    Scratch<T> S;
+    NM_TRY(get_scratch<T>(P, b, S));
+    Mats<T> m = mats<T>(P);
+    const ChebCoef cc(mlo, mhi);
+    NM_TRY(launch_scale_copy<T>(n, b, (T)f->gamma[0], Y, ldy, Z, ldz, s));
+    if (d == 0) return NM_OK;
+    NM_TRY(launch_scale_copy<T>(n, b, (T)1, Y, ldy, S.TA, b, s));
+    T* cur = S.TA;   // T_k
+    T* prev = S.TB;  // T_{k-1}
+    const int64_t kl = 1 + (P->info.Np > 0 ? f->k_P : 0);
+    for (int k = 0; k < d; ++k) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        NM_TRY(prof_begin(P, s, &e0));
+        NM_TRY(apply_K_t<T>(P, cur, b, S.W, b, b, f->k_P, S, S.XA, cc.inv_theta, s));
+        NM_TRY(prof_end(P, s, 1, e0, kl));
+        NM_TRY(prof_begin(P, s, &e1));
+        FiltStep fs;
+        fs.cshift = f->c;
+        fs.gam = f->gamma[k + 1];
+        if (k == 0) {
+            fs.a1 = 1.0 / f->e;
+            fs.a2 = 0.0;
+            NM_TRY(mass_steps<T>(m, b, f->k_M, mlo, mhi, S, &fs, cur, nullptr, prev, Z, ldz, nullptr, 0, s));
+        } else {
+            fs.a1 = 2.0 / f->e;
+            fs.a2 = 1.0;
+            NM_TRY(mass_steps<T>(m, b, f->k_M, mlo, mhi, S, &fs, cur, prev, prev, Z, ldz, nullptr, 0, s));
+        }
+        NM_TRY(prof_end(P, s, 0, e1, f->k_M - 1));
+        std::swap(cur, prev);
+    }
+    return NM_OK;
+}
+
+// ------------------------------------------------------------------ mixed precision
+// Scratch: doubles TA, TB, W (n x b), S64, Q64 (Np x b); floats w32, xa, xb,
+// xs, es (n x b; the pressure solve reuses their first Np x b entries).
+struct MixScratch {
+    double *TA, *TB, *W, *S64, *Q64;
+    float *w32, *xa, *xb, *xs, *es;
+};
+
+static int get_mix_scratch(nm_problem* P, int b, MixScratch& S) {
+    const int64_t n = P->info.n, Np = P->info.Np;
+    const size_t need = (size_t)(3 * n + 2 * Np) * b * sizeof(double) + (size_t)5 * n * b * sizeof(float);
+    if (P->ws.bytes < need) {
+        P->ws.buf.release();
+        NM_TRY(P->ws.buf.alloc(need));
+        P->ws.bytes = need;
+    }
+    double* d = P->ws.buf.as<double>();
+    S.TA = d; d += n * b;
+    S.TB = d; d += n * b;
+    S.W = d; d += n * b;
+    S.S64 = d; d += Np * b;
+    S.Q64 = d; d += Np * b;
+    float* f = reinterpret_cast<float*>(d);
+    S.w32 = f; f += n * b;
+    S.xa = f; f += n * b;
+    S.xb = f; f += n * b;
+    S.xs = f; f += n * b;
+    S.es = f;
+    return NM_OK;
+}
+
+// k steps of float Jacobi-Chebyshev semi-iteration for (A (x) I_R) x = w;
+// w, xa, xb, xout: (R nodes) x b floats with ld b, xout distinct from xa, xb.
+static int cheb32(const DevCSR& A, int R, int b, int k, double lo, double hi, const float* w, float* xa,
+                  float* xb, float* xout, cudaStream_t s) {
+    const ChebCoef cc(lo, hi);
+    const int64_t nodes = A.nrows;
+    if (k == 1) return launch_dscale<float>(R, nodes, b, (float)cc.inv_theta, A.dinv32.as<float>(), w, b, xout, b, s);
+    NM_TRY(launch_dscale<float>(R, nodes, b, (float)cc.inv_theta, A.dinv32.as<float>(), w, b, xa, b, s));
+    float* buf[2] = {xb, xa};
+    double om = 2.0;
+    for (int j = 2; j <= k; ++j) {
+        om = 1.0 / (1.0 - om / cc.four_sig2);
+        KronArgs<float> a;
+        a.nrows = (int)nodes;
+        a.rowptr = A.rowptr.as<int>();
+        a.col = A.col.as<int>();
+        a.val = A.val32.as<float>();
+        a.dinv = A.dinv32.as<float>();
+        a.b = b;
+        a.X = buf[(j - 1) & 1];
+        a.ldx = b;
+        a.W = w;
+        a.ldw = b;
+        a.Xp = j == 2 ? nullptr : buf[j & 1];
+        a.ldp = b;
+        a.Xn = j == k ? xout : buf[j & 1];
+        a.ldn = b;
+        a.om = (float)om;
+        a.inv_theta = (float)cc.inv_theta;
+        NM_TRY(launch_kron<float>(R, KRON_CHEB, a, s));
+    }
+    return NM_OK;
+}
+
+// Refined solve: x = P32 w, r = w - A x (double), e = P32 r; leaves x in
+// S.xs and e in S.es (the caller combines them).
+static int mixed_solve(const DevCSR& A, int R, int b, int k, const double* W, int64_t ldw, const MixScratch& S,
+                       cudaStream_t s) {
+    const int64_t rows = R * A.nrows;
+    NM_TRY((launch_convert<double, float>(rows, b, W, ldw, S.w32, b, s)));
+    NM_TRY(cheb32(A, R, b, k, kMassLo, kMassHi, S.w32, S.xa, S.xb, S.xs, s));
+    NM_TRY(launch_resid_mixed(R, A.nrows, A.rowptr.as<int>(), A.col.as<int>(), A.val.as<double>(), W, ldw, S.xs,
+                              S.w32, b, s));
+    return cheb32(A, R, b, k, kMassLo, kMassHi, S.w32, S.xa, S.xb, S.es, s);
+}
+
+// W = K_eff X in double with the pressure inverse by a refined solve.
+static int apply_K_mixed(nm_problem* P, const double* X, int64_t ldx, double* W, int64_t ldw, int b, int k_P,
+                         const MixScratch& S, cudaStream_t s) {
+    Mats<double> m = mats<double>(P);
+    Bsr33Args<double> a;
+    a.nrows = (int)m.Nu;
+    a.rowptr = m.u_rp;
+    a.col = m.u_col;
+    a.val = m.AG;
+    a.b = b;
+    a.X = X;
+    a.ldx = ldx;
+    a.W = W;
+    a.ldw = ldw;
+    if (m.Np > 0) {
+        Bsr13Args<double> q;
+        q.nrows = (int)m.Np;
+        q.rowptr = m.et_rp;
+        q.col = m.et_col;
+        q.val = m.EGt;
+        q.b = b;
+        q.X = X;
+        q.ldx = ldx;
+        q.Q = S.Q64;
+        q.ldq = b;
+        NM_TRY(launch_bsr13<double>(q, s));
+        NM_TRY(mixed_solve(P->Pn, 1, b, k_P, S.Q64, b, S, s));
+        CombineArgs c;
+        c.rows = m.Np;
+        c.b = b;
+        c.x32 = S.xs;
+        c.e32 = S.es;
+        c.out = S.S64;
+        NM_TRY(launch_combine(c, s));
+        a.e_rowptr = m.e_rp;
+        a.e_col = m.e_col;
+        a.e_val = m.EG;
+        a.S = S.S64;
+        a.lds = b;
+    }
+    return launch_bsr33<double>(a, s);
+}
+
+static int filter_apply_mixed(nm_problem* P, const nm_filter* f, const double* Y, int64_t ldy, double* Z,
+                              int64_t ldz, int b, cudaStream_t s) {
+    const int d = f->degree;
+    if (d < 0 || !f->gamma) return fail(NM_EINVAL, "filter needs degree >= 0 and gamma");
+    if (f->k_M < 1 || (P->info.Np > 0 && f->k_P < 1)) return fail(NM_EINVAL, "k_M and k_P must be >= 1");
+    if (!(f->e > 0)) return fail(NM_EINVAL, "filter half-width e must be positive");
+    if (f->m_lo > 0 || f->m_hi > 0) return fail(NM_EUNSUPPORTED, "mixed mode uses the P2 element bounds");
+    NM_TRY(ensure_f32(P, s));
+    const int64_t n = P->info.n;
+    MixScratch S;
+    NM_TRY(get_mix_scratch(P, b, S));
+    NM_TRY(launch_scale_copy<double>(n, b, f->gamma[0], Y, ldy, Z, ldz, s));
+    if (d == 0) return NM_OK;
+    NM_TRY(launch_scale_copy<double>(n, b, 1.0, Y, ldy, S.TA, b, s));
+    double* cur = S.TA;
+    double* prev = S.TB;
+    const int64_t kl = 1 + (P->info.Np > 0 ? 2 * f->k_P + 4 : 0);
+    for (int k = 0; k < d; ++k) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        NM_TRY(prof_begin(P, s, &e0));
+        NM_TRY(apply_K_mixed(P, cur, b, S.W, b, b, f->k_P, S, s));
+        NM_TRY(prof_end(P, s, 1, e0, kl));
+        NM_TRY(prof_begin(P, s, &e1));
+        NM_TRY(mixed_solve(P->Mr, 3, b, f->k_M, S.W, b, S, s));
+        CombineArgs c;
+        c.rows = n;
+        c.b = b;
+        c.x32 = S.xs;
+        c.e32 = S.es;
+        c.Tk = cur;
+        c.Tp = k == 0 ? nullptr : prev;
+        c.Tn = prev;
+        c.Z = Z;
+        c.ldz = ldz;
+        c.a1 = (k == 0 ? 1.0 : 2.0) / f->e;
+        c.cshift = f->c;
+        c.a2 = k == 0 ? 0.0 : 1.0;
+        c.gam = f->gamma[k + 1];
+        NM_TRY(launch_combine(c, s));
+        NM_TRY(prof_end(P, s, 0, e1, 2 * f->k_M + 3));
+        std::swap(cur, prev);
+    }
+    return NM_OK;
+}
+
+int filter_apply_mixed_pub(nm_problem* P, const nm_filter* f, const double* Y, int64_t ldy, double* Z, int64_t ldz,
+                           int b, cudaStream_t s) {
+    return filter_apply_mixed(P, f, Y, ldy, Z, ldz, b, s);
+}
+
+int apply_K_mixed_pub(nm_problem* P, const double* X, int64_t ldx, double* Y, int64_t ldy, int b, int k_P,
+                      cudaStream_t s) {
+    NM_TRY(ensure_f32(P, s));
+    MixScratch S;
+    NM_TRY(get_mix_scratch(P, b, S));
+    return apply_K_mixed(P, X, ldx, Y, ldy, b, k_P, S, s);
+}
+
+int solve_M_mixed_pub(nm_problem* P, int k_M, const double* W, int64_t ldw, double* X, int64_t ldx, int b,
+                      cudaStream_t s) {
+    NM_TRY(ensure_f32(P, s));
+    MixScratch S;
+    NM_TRY(get_mix_scratch(P, b, S));
+    NM_TRY(mixed_solve(P->Mr, 3, b, k_M, W, ldw, S, s));
+    CombineArgs c;
+    c.rows = P->info.n;
+    c.b = b;
+    c.x32 = S.xs;
+    c.e32 = S.es;
+    c.out = S.W;
+    NM_TRY(launch_combine(c, s));
+    return launch_scale_copy<double>(P->info.n, b, 1.0, S.W, b, X, ldx, s);
+}
+
+// ------------------------------------------------------------------ profiling
+int prof_begin(nm_problem* P, cudaStream_t s, cudaEvent_t* start) {
+    *start = nullptr;
+    if (!P->profile) return NM_OK;
+    if (P->ev_next + 2 > P->ev_pool.size()) {
+        for (int i = 0; i < 256; ++i) {
+            cudaEvent_t e;
+            NM_CUDA(cudaEventCreate(&e));
+            P->ev_pool.push_back(e);
+        }
+    }
+    *start = P->ev_pool[P->ev_next++];
+    NM_CUDA(cudaEventRecord(*start, s));
+    return NM_OK;
+}
+
+int prof_end(nm_problem* P, cudaStream_t s, int kind, cudaEvent_t start, int64_t launches) {
+    if (!P->profile || !start) return NM_OK;
+    cudaEvent_t stop = P->ev_pool[P->ev_next++];
+    NM_CUDA(cudaEventRecord(stop, s));
+    P->ev_regions.push_back({kind, {start, stop}});
+    P->ev_launches.push_back(launches);
+    return NM_OK;
+}
+
+int profile_read(nm_problem* P, int kind, int64_t* launches, double* ms) {
+    int64_t l = 0;
+    double t = 0.0;
+    for (size_t i = 0; i < P->ev_regions.size(); ++i) {
+        if (P->ev_regions[i].first != kind) continue;
+        NM_CUDA(cudaEventSynchronize(P->ev_regions[i].second.second));
+        float x = 0.f;
+        NM_CUDA(cudaEventElapsedTime(&x, P->ev_regions[i].second.first, P->ev_regions[i].second.second));
+        t += x;
+        l += P->ev_launches[i];
+    }
+    *launches = l;
+    *ms = t;
+    return NM_OK;
+}
+
+int profile_set(nm_problem* P, int enable, int reset) {
+    if (reset || !enable) {
+        // fold nothing: a reset discards the recorded regions (events are reused)
+        for (auto& r : P->ev_regions) {
+            cudaEventSynchronize(r.second.second);
+        }
+        P->ev_regions.clear();
+        P->ev_launches.clear();
+        P->ev_next = 0;
+    }
+    P->profile = enable;
+    return NM_OK;
+}
+
+// ------------------------------------------------------------------ public pieces
+template <typename T>
+int apply_K_pub(nm_problem* P, const T* X, int64_t ldx, T* Y, int64_t ldy, int b, int k_P, cudaStream_t s) {
+    Scratch<T> S;
+    NM_TRY(get_scratch<T>(P, b, S));
+    return apply_K_t<T>(P, X, ldx, Y, ldy, b, k_P, S, nullptr, 0.0, s);
+}
+
+template <typename T>
+int apply_M_pub(nm_problem* P, const T* X, int64_t ldx, T* Y, int64_t ldy, int b, int mode,
+                const double* sk, cudaStream_t s) {
+    Mats<T> m = mats<T>(P);
+    KronArgs<T> a;
+    a.nrows = (int)m.Nu;
+    a.rowptr = m.u_rp;
+    a.col = m.u_col;
+    a.val = m.Mr;
+    a.b = b;
+    a.X = X;
+    a.ldx = ldx;
+    a.Y = Y;
+    a.ldy = ldy;
+    if (sk)
+        for (int i = 0; i < 9; ++i) a.sk[i] = (T)sk[i];
+    return launch_kron<T>(3, mode, a, s);
+}
+
+template <typename T>
+__global__ void dscale_kernel(int64_t Nu, int b, T inv_theta, const T* dinv, const T* W, int64_t ldw,
+                              T* X, int64_t ldx) {
+    const int64_t total = 3 * Nu * b;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / b;
+        const int c = (int)(t - r * b);
+        X[r * ldx + c] = inv_theta * dinv[r / 3] * W[r * ldw + c];
+    }
+}
+
+template <typename T>
+int solve_M_pub(nm_problem* P, int k_M, double lo, double hi, const T* W, int64_t ldw, T* X,
+                int64_t ldx, int b, cudaStream_t s) {
+    if (k_M < 1) return fail(NM_EINVAL, "k_M must be >= 1");
+    const double mlo = lo > 0 ? lo : kMassLo, mhi = hi > 0 ? hi : kMassHi;
+    if (!(mhi > mlo)) return fail(NM_EINVAL, "mass bounds need hi > lo > 0");
+    Scratch<T> S;
+    NM_TRY(get_scratch<T>(P, b, S));
+    Mats<T> m = mats<T>(P);
+    const ChebCoef cc(mlo, mhi);
+    const int64_t n = P->info.n;
+    int64_t g = (n * b + 255) / 256;
+    if (g > 4864) g = 4864;
+    if (k_M == 1) {
+        dscale_kernel<T><<<(unsigned)g, 256, 0, s>>>(m.Nu, b, (T)cc.inv_theta, m.dM, W, ldw, X, ldx);
+        count_launch();
+        NM_CUDA(cudaGetLastError());
+        return NM_OK;
+    }
+    // W is the right-hand side of every step: copy it into the scratch slot
+    NM_TRY(launch_scale_copy<T>(n, b, (T)1, W, ldw, S.W, b, s));
+    dscale_kernel<T><<<(unsigned)g, 256, 0, s>>>(m.Nu, b, (T)cc.inv_theta, m.dM, S.W, b, S.XA, b);
+    count_launch();
+        NM_CUDA(cudaGetLastError());
+    return mass_steps<T>(m, b, k_M, mlo, mhi, S, nullptr, nullptr, nullptr, nullptr, nullptr, 0, X, ldx, s);
+}
+
+template int filter_apply_t<double>(nm_problem*, const nm_filter*, const double*, int64_t, double*, int64_t, int, cudaStream_t);
+template int filter_apply_t<float>(nm_problem*, const nm_filter*, const float*, int64_t, float*, int64_t, int, cudaStream_t);
+template int apply_K_pub<double>(nm_problem*, const double*, int64_t, double*, int64_t, int, int, cudaStream_t);
+template int apply_K_pub<float>(nm_problem*, const float*, int64_t, float*, int64_t, int, int, cudaStream_t);
+template int apply_M_pub<double>(nm_problem*, const double*, int64_t, double*, int64_t, int, int, const double*, cudaStream_t);
+template int apply_M_pub<float>(nm_problem*, const float*, int64_t, float*, int64_t, int, int, const double*, cudaStream_t);
+template int solve_M_pub<double>(nm_problem*, int, double, double, const double*, int64_t, double*, int64_t, int, cudaStream_t);
+template int solve_M_pub<float>(nm_problem*, int, double, double, const float*, int64_t, float*, int64_t, int, cudaStream_t);
+
+// ------------------------------------------------------------------ filter design
+void jackson_step_coeffs(double lam_lo, double lam_hi, double xi, double eta, int d, double* gamma,
+                         double* c, double* e) {
+    *c = 0.5 * (lam_hi + lam_lo);
+    *e = 0.5 * (lam_hi - lam_lo);
+    double al = (xi - *c) / *e, be = (eta - *c) / *e;
+    al = std::min(1.0, std::max(-1.0, al));
+    be = std::min(1.0, std::max(-1.0, be));
+    const double ta = std::acos(al), tb = std::acos(be);
+    const double ad = M_PI / (d + 2);
+    for (int k = 0; k <= d; ++k) {
+        const double mu = k == 0 ? (ta - tb) / M_PI : 2.0 * (std::sin(k * ta) - std::sin(k * tb)) / (k * M_PI);
+        const double g = ((1.0 - (double)k / (d + 2)) * std::sin(ad) * std::cos(k * ad) +
+                          std::cos(ad) * std::sin(k * ad) / (d + 2)) / std::sin(ad);
+        gamma[k] = g * mu;
+    }
+}
+
+static double cheb_sum(const std::vector<double>& g, double t) {
+    t = std::min(1.0, std::max(-1.0, t));
+    double T0 = 1, T1 = t, s = g[0];
+    if (g.size() > 1) s += g[1] * T1;
+    for (size_t k = 2; k < g.size(); ++k) {
+        const double T2 = 2 * t * T1 - T0;
+        s += g[k] * T2;
+        T0 = T1;
+        T1 = T2;
+    }
+    return s;
+}
+
+// ------------------------------------------------------------------ dense helpers
+struct Dense {
+    nm_ctx* ctx;
+    cudaStream_t s;
+};
+
+// C (m x b, col-major) = V^T (M W): V row-major n x m (ld ldv), MW row-major n x b (ld b)
+static int gemm_VtW(nm_ctx* ctx, int64_t n, int m, int b, const double* V, int64_t ldv,
+                    const double* MW, int64_t ldw, double* C, double beta) {
+    const double one = 1.0;
+    NM_CUBLAS(cublasDgemm(ctx->cublas, CUBLAS_OP_N, CUBLAS_OP_T, m, b, (int)n, &one, V, (int)ldv, MW,
+                          (int)ldw, &beta, C, m));
+    return NM_OK;
+}
+
+// W (row-major n x b, ld ldw) += alpha * V C, C col-major m x b
+static int gemm_WmVC(nm_ctx* ctx, int64_t n, int m, int b, double alpha, const double* V, int64_t ldv,
+                     const double* C, int ldc, double* W, int64_t ldw) {
+    const double one = 1.0;
+    NM_CUBLAS(cublasDgemm(ctx->cublas, CUBLAS_OP_T, CUBLAS_OP_N, b, (int)n, m, &alpha, C, ldc, V,
+                          (int)ldv, &one, W, (int)ldw));
+    return NM_OK;
+}
+
+template <typename T>
+struct OpBuf {
+    DevBuf f_in, f_out;   // float staging for the FP32 filter
+};
+
+// W = p(B) V_j (prec selects the filter arithmetic); V_j, W FP64 row-major
+static int filter_block(nm_problem* P, const nm_filter* f, const double* Vj, int64_t ldv, double* W,
+                        int b, nm_prec prec, DevBuf& fin, DevBuf& fout, cudaStream_t s) {
+    const int64_t n = P->info.n;
+    if (prec == NM_F64) return filter_apply_t<double>(P, f, Vj, ldv, W, b, b, s);
+    if (prec == NM_MIXED) return filter_apply_mixed(P, f, Vj, ldv, W, b, b, s);
+    NM_TRY(ensure_f32(P, s));
+    if (fin.bytes < (size_t)n * b * sizeof(float)) {
+        fin.release();
+        fout.release();
+        NM_TRY(fin.alloc((size_t)n * b * sizeof(float)));
+        NM_TRY(fout.alloc((size_t)n * b * sizeof(float)));
+    }
+    NM_TRY((launch_convert<double, float>(n, b, Vj, ldv, fin.as<float>(), b, s)));
+    NM_TRY(filter_apply_t<float>(P, f, fin.as<float>(), b, fout.as<float>(), b, b, s));
+    return launch_convert<float, double>(n, b, fout.as<float>(), b, W, b, s);
+}
+
+// Apply K_eff (FP64, effectively exact Schur term) or M to m columns of a
+// row-major n x m block in chunks of <= 64 columns.
+static int apply_cols(nm_problem* P, int which, const double* V, int64_t ldv, double* Y, int64_t ldy,
+                      int m, int k_P, cudaStream_t s) {
+    for (int c0 = 0; c0 < m; c0 += 64) {
+        const int bc = std::min(64, m - c0);
+        if (which == 0)
+            NM_TRY(apply_K_pub<double>(P, V + c0, ldv, Y + c0, ldy, bc, k_P, s));
+        else if (which == 1)
+            NM_TRY(apply_M_pub<double>(P, V + c0, ldv, Y + c0, ldy, bc, KRON_PLAIN, nullptr, s));
+        else {
+            const double* O = P->Omega;
+            const double sk[9] = {0, -O[2], O[1], O[2], 0, -O[0], -O[1], O[0], 0};
+            NM_TRY(apply_M_pub<double>(P, V + c0, ldv, Y + c0, ldy, bc, KRON_CORI, sk, s));
+        }
+    }
+    return NM_OK;
+}
+
+// Symmetric dense eigensolve on the device: A (m x m col-major, overwritten by
+// eigenvectors), w (m). With B != nullptr the generalized problem A x = w B x.
+static int dense_eig(nm_ctx* ctx, int m, double* A, double* B, double* w) {
+    int lwork = 0;
+    DevBuf info;
+    NM_TRY(info.alloc(sizeof(int)));
+    if (B) {
+        NM_CUSOLVER(cusolverDnDsygvd_bufferSize(ctx->cusolver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                                                CUBLAS_FILL_MODE_UPPER, m, A, m, B, m, w, &lwork));
+        DevBuf work;
+        NM_TRY(work.alloc(std::max(lwork, 1) * sizeof(double)));
+        NM_CUSOLVER(cusolverDnDsygvd(ctx->cusolver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                                     CUBLAS_FILL_MODE_UPPER, m, A, m, B, m, w, work.as<double>(), lwork,
+                                     info.as<int>()));
+    } else {
+        NM_CUSOLVER(cusolverDnDsyevd_bufferSize(ctx->cusolver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER,
+                                                m, A, m, w, &lwork));
+        DevBuf work;
+        NM_TRY(work.alloc(std::max(lwork, 1) * sizeof(double)));
+        NM_CUSOLVER(cusolverDnDsyevd(ctx->cusolver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, m, A, m,
+                                     w, work.as<double>(), lwork, info.as<int>()));
+    }
+    int h = 0;
+    NM_CUDA(cudaMemcpyAsync(&h, info.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    NM_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (h != 0) return fail(NM_ENOTCONV, "dense eigensolver failed, info = " + std::to_string(h));
+    return NM_OK;
+}
+
+__global__ void symmetrize_kernel(int m, double* A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i < m && j < i) {
+        const double v = 0.5 * (A[i + (int64_t)j * m] + A[j + (int64_t)i * m]);
+        A[i + (int64_t)j * m] = v;
+        A[j + (int64_t)i * m] = v;
+    }
+}
+
+static int symmetrize(int m, double* A, cudaStream_t s) {
+    dim3 g((m + 127) / 128, m);
+    symmetrize_kernel<<<g, 128, 0, s>>>(m, A);
+    count_launch();
+        NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+// M-orthonormalise W (row-major n x b) in place with Cholesky-QR; R (b x b col-major upper) out.
+static int m_orth(nm_problem* P, double* W, int64_t ldw, int b, double* MW, double* G, int* rank_ok,
+                  cudaStream_t s) {
+    nm_ctx* ctx = P->ctx;
+    const int64_t n = P->info.n;
+    NM_TRY(apply_M_pub<double>(P, W, ldw, MW, b, b, KRON_PLAIN, nullptr, s));
+    NM_TRY(gemm_VtW(ctx, n, b, b, W, ldw, MW, b, G, 0.0));
+    NM_TRY(symmetrize(b, G, s));
+    int lwork = 0;
+    NM_CUSOLVER(cusolverDnDpotrf_bufferSize(ctx->cusolver, CUBLAS_FILL_MODE_UPPER, b, G, b, &lwork));
+    DevBuf work, info;
+    NM_TRY(work.alloc(std::max(lwork, 1) * sizeof(double)));
+    NM_TRY(info.alloc(sizeof(int)));
+    NM_CUSOLVER(cusolverDnDpotrf(ctx->cusolver, CUBLAS_FILL_MODE_UPPER, b, G, b, work.as<double>(), lwork,
+                                 info.as<int>()));
+    int h = 0;
+    NM_CUDA(cudaMemcpyAsync(&h, info.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NM_CUDA(cudaStreamSynchronize(s));
+    *rank_ok = h == 0;
+    if (h != 0) return NM_OK;
+    // W <- W R^{-1}: in column-major terms Wc (b x n) <- R^{-T} Wc
+    const double one = 1.0;
+    NM_CUBLAS(cublasDtrsm(ctx->cublas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T,
+                          CUBLAS_DIAG_NON_UNIT, b, (int)n, &one, G, b, W, (int)ldw));
+    return NM_OK;
+}
+
+struct RRResult {
+    std::vector<double> lam, res;
+    int i0 = 0, k = 0;
+};
+
+// Rayleigh-Ritz of (K_eff, M) on V (n x m row-major, ld ldv, FP64). If X is
+// non-null the selected Ritz vectors are written there (n x k, ld k).
+static int rayleigh_ritz(nm_problem* P, const double* V, int64_t ldv, int m, double lam_lo, double lam_hi,
+                         DevBuf* X, RRResult& out) {
+    nm_ctx* ctx = P->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t n = P->info.n;
+    DevBuf KV, MV, H, G, w;
+    NM_TRY(KV.alloc((size_t)n * m * sizeof(double)));
+    NM_TRY(MV.alloc((size_t)n * m * sizeof(double)));
+    NM_TRY(H.alloc((size_t)m * m * sizeof(double)));
+    NM_TRY(G.alloc((size_t)m * m * sizeof(double)));
+    NM_TRY(w.alloc((size_t)m * sizeof(double)));
+    NM_TRY(apply_cols(P, 0, V, ldv, KV.as<double>(), m, m, 80, s));
+    NM_TRY(apply_cols(P, 1, V, ldv, MV.as<double>(), m, m, 0, s));
+    NM_TRY(gemm_VtW(ctx, n, m, m, V, ldv, KV.as<double>(), m, H.as<double>(), 0.0));
+    NM_TRY(gemm_VtW(ctx, n, m, m, V, ldv, MV.as<double>(), m, G.as<double>(), 0.0));
+    NM_TRY(symmetrize(m, H.as<double>(), s));
+    NM_TRY(symmetrize(m, G.as<double>(), s));
+    NM_TRY(dense_eig(ctx, m, H.as<double>(), G.as<double>(), w.as<double>()));
+    std::vector<double> hw(m);
+    NM_CUDA(cudaMemcpyAsync(hw.data(), w.p, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NM_CUDA(cudaStreamSynchronize(s));
+    int i0 = 0;
+    while (i0 < m && hw[i0] < lam_lo) ++i0;
+    int i1 = i0;
+    while (i1 < m && hw[i1] <= lam_hi) ++i1;
+    const int k = i1 - i0;
+    out.i0 = i0;
+    out.k = k;
+    out.lam.assign(hw.begin() + i0, hw.begin() + i1);
+    out.res.assign(k, 0.0);
+    if (k == 0) return NM_OK;
+    const double* Ssel = H.as<double>() + (int64_t)i0 * m;   // eigenvectors, col-major m x m
+    DevBuf KX, MX, lam_d, nr, nm_;
+    NM_TRY(KX.alloc((size_t)n * k * sizeof(double)));
+    NM_TRY(MX.alloc((size_t)n * k * sizeof(double)));
+    NM_TRY(lam_d.alloc(k * sizeof(double)));
+    NM_TRY(nr.alloc(k * sizeof(double)));
+    NM_TRY(nm_.alloc(k * sizeof(double)));
+    const double one = 1.0, zero = 0.0;
+    // Xc (k x n) = S_sel^T Vc
+    auto proj = [&](const double* Vsrc, int64_t ld, double* dst) -> int {
+        NM_CUBLAS(cublasDgemm(ctx->cublas, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)n, m, &one, Ssel, m, Vsrc, (int)ld,
+                              &zero, dst, k));
+        return NM_OK;
+    };
+    NM_TRY(proj(KV.as<double>(), m, KX.as<double>()));
+    NM_TRY(proj(MV.as<double>(), m, MX.as<double>()));
+    NM_CUDA(cudaMemcpyAsync(lam_d.p, out.lam.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+    NM_TRY(launch_resid_block(n, k, KX.as<double>(), MX.as<double>(), lam_d.as<double>(), KX.as<double>(), s));
+    NM_CUDA(cudaMemsetAsync(nr.p, 0, k * sizeof(double), s));
+    NM_CUDA(cudaMemsetAsync(nm_.p, 0, k * sizeof(double), s));
+    NM_TRY(launch_colnorm2(n, k, KX.as<double>(), k, nr.as<double>(), s));
+    NM_TRY(launch_colnorm2(n, k, MX.as<double>(), k, nm_.as<double>(), s));
+    std::vector<double> hr(k), hm(k);
+    NM_CUDA(cudaMemcpyAsync(hr.data(), nr.p, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NM_CUDA(cudaMemcpyAsync(hm.data(), nm_.p, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NM_CUDA(cudaStreamSynchronize(s));
+    const double floor = 1e-3 * std::max(std::fabs(lam_lo), std::fabs(lam_hi));
+    for (int i = 0; i < k; ++i)
+        out.res[i] = std::sqrt(hr[i]) / (std::sqrt(hm[i]) * std::max(std::fabs(out.lam[i]), floor));
+    if (X) {
+        NM_TRY(X->alloc((size_t)n * k * sizeof(double)));
+        NM_TRY(proj(V, ldv, X->as<double>()));
+        NM_CUDA(cudaStreamSynchronize(s));
+    }
+    return NM_OK;
+}
+
+// ------------------------------------------------------------------ bounds
+int spectrum_bounds(nm_problem* P, int steps, int k_M, uint64_t seed, double* lam_lo, double* lam_hi) {
+    nm_ctx* ctx = P->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t n = P->info.n;
+    if (steps < 2) steps = 40;
+    if (k_M < 2) k_M = 57;
+    const int ldv = steps + 1;
+    DevBuf V, W, MW, C, G, tmp;
+    NM_TRY(V.alloc((size_t)n * ldv * sizeof(double)));
+    NM_TRY(W.alloc((size_t)n * sizeof(double)));
+    NM_TRY(MW.alloc((size_t)n * sizeof(double)));
+    NM_TRY(C.alloc((size_t)ldv * sizeof(double)));
+    NM_TRY(G.alloc(sizeof(double)));
+    NM_TRY(tmp.alloc((size_t)n * sizeof(double)));
+    NM_TRY(launch_philox_normal(n, seed, tmp.as<double>(), s));
+    NM_TRY(launch_scale_copy<double>(n, 1, 1.0, tmp.as<double>(), 1, V.as<double>(), ldv, s));
+    int ok = 1;
+    NM_TRY(m_orth(P, V.as<double>(), ldv, 1, MW.as<double>(), G.as<double>(), &ok, s));
+    if (!ok) return fail(NM_ENOTCONV, "start vector has zero M-norm");
+    std::vector<double> T((size_t)steps * steps, 0.0);
+    double beta_last = 0.0;
+    int done = 0;
+    Scratch<double> S;
+    NM_TRY(get_scratch<double>(P, 1, S));
+    for (int j = 0; j < steps; ++j) {
+        const double* vj = V.as<double>() + j;
+        // w = P_M K v_j
+        NM_TRY(apply_K_t<double>(P, vj, ldv, S.W, 1, 1, k_M, S, S.XA, 1.0 / (0.5 * (kMassLo + kMassHi)), s));
+        NM_TRY(mass_steps<double>(mats<double>(P), 1, k_M, kMassLo, kMassHi, S, nullptr, nullptr, nullptr,
+                                  nullptr, nullptr, 0, W.as<double>(), 1, s));
+        std::vector<double> hsum(j + 1, 0.0), hc(j + 1);
+        for (int pass = 0; pass < 2; ++pass) {
+            NM_TRY(apply_M_pub<double>(P, W.as<double>(), 1, MW.as<double>(), 1, 1, KRON_PLAIN, nullptr, s));
+            NM_TRY(gemm_VtW(ctx, n, j + 1, 1, V.as<double>(), ldv, MW.as<double>(), 1, C.as<double>(), 0.0));
+            NM_TRY(gemm_WmVC(ctx, n, j + 1, 1, -1.0, V.as<double>(), ldv, C.as<double>(), j + 1, W.as<double>(), 1));
+            NM_CUDA(cudaMemcpyAsync(hc.data(), C.p, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+            NM_CUDA(cudaStreamSynchronize(s));
+            for (int i = 0; i <= j; ++i) hsum[i] += hc[i];
+        }
+        for (int i = 0; i <= j; ++i) T[(size_t)i + (size_t)j * steps] = hsum[i];
+        NM_TRY(launch_scale_copy<double>(n, 1, 1.0, W.as<double>(), 1, V.as<double>() + j + 1, ldv, s));
+        NM_TRY(m_orth(P, V.as<double>() + j + 1, ldv, 1, MW.as<double>(), G.as<double>(), &ok, s));
+        double g = 0;
+        NM_CUDA(cudaMemcpyAsync(&g, G.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        NM_CUDA(cudaStreamSynchronize(s));
+        beta_last = ok ? g : 0.0;
+        done = j + 1;
+        if (!ok) break;
+    }
+    // eigenvalues of the symmetrised projected matrix (host-tiny, done on device)
+    const int m = done;
+    std::vector<double> Tm((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            const double a = i <= j ? T[(size_t)i + (size_t)j * steps] : T[(size_t)j + (size_t)i * steps];
+            Tm[(size_t)i + (size_t)j * m] = a;
+        }
+    DevBuf Td, wd;
+    NM_TRY(Td.alloc((size_t)m * m * sizeof(double)));
+    NM_TRY(wd.alloc((size_t)m * sizeof(double)));
+    NM_CUDA(cudaMemcpy(Td.p, Tm.data(), Tm.size() * sizeof(double), cudaMemcpyHostToDevice));
+    NM_TRY(dense_eig(ctx, m, Td.as<double>(), nullptr, wd.as<double>()));
+    std::vector<double> th(m), Sv((size_t)m * m);
+    NM_CUDA(cudaMemcpy(th.data(), wd.p, m * sizeof(double), cudaMemcpyDeviceToHost));
+    NM_CUDA(cudaMemcpy(Sv.data(), Td.p, Sv.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    const double r_hi = std::fabs(beta_last * Sv[(size_t)(m - 1) + (size_t)(m - 1) * m]);
+    const double r_lo = std::fabs(beta_last * Sv[(size_t)(m - 1)]);
+    // Upper end: Ritz value plus its residual bound, 1% margin. Lower end:
+    // the smallest Ritz value (an upper bound of lambda_min) moved down by
+    // 1e-6 lam_hi. The residual of the bottom Ritz value is not used: at the
+    // clustered low end it is large and would push lam_lo far below the
+    // spectrum, costing filter resolution exactly where slices sit; an
+    // undershoot of delta only lets T_d grow to cosh(d sqrt(2 delta / e)),
+    // about 1 for delta << e / d^2.
+    (void)r_lo;
+    const double hi = (th[m - 1] + r_hi) * 1.01;
+    const double lo = std::min(0.0, th[0]) - 1e-6 * hi;
+    *lam_lo = lo;
+    *lam_hi = hi;
+    P->bounds_lo = lo;
+    P->bounds_hi = hi;
+    P->have_bounds = 1;
+    return NM_OK;
+}
+
+// ------------------------------------------------------------------ Lanczos
+int lanczos_slice(nm_problem* P, const nm_slice_opts* o, nm_result** out) {
+    auto t_start = std::chrono::steady_clock::now();
+    nm_ctx* ctx = P->ctx;
+    cudaStream_t s = ctx->stream;
+    if (!P->have_interval) return fail(NM_EINVAL, "call nm_set_interval first");
+    const int b = o->block;
+    if (b < 1 || b > 64) return fail(NM_EINVAL, "block must be in 1..64");
+    if (o->degree < 1) return fail(NM_EINVAL, "degree must be >= 1");
+    if (o->max_blocks < 2) return fail(NM_EINVAL, "max_blocks must be >= 2");
+    const int k_M = o->k_M > 0 ? o->k_M : 57;
+    const int k_P = o->k_P > 0 ? o->k_P : 57;
+    const double tol = o->tol > 0 ? o->tol : 1e-6;
+    const int check = o->check_every > 0 ? o->check_every : 1;
+    const int64_t n = P->info.n;
+    double blo, bhi;
+    NM_TRY(spectrum_bounds(P, o->bounds_steps > 0 ? o->bounds_steps : 40, k_M, o->seed + 1, &blo, &bhi));
+    const double lam_lo = P->lo <= 0 ? -1e-8 * bhi : P->lo;
+    const double lam_hi = P->hi;
+    std::vector<double> gamma(o->degree + 1);
+    double c, e;
+    jackson_step_coeffs(blo, bhi, lam_lo, lam_hi, o->degree, gamma.data(), &c, &e);
+    const double pa = cheb_sum(gamma, (lam_lo - c) / e), pb = cheb_sum(gamma, (lam_hi - c) / e);
+    const double tau = lam_lo > blo ? 0.8 * std::min(pa, pb) : 0.8 * pb;
+    nm_filter f{o->degree, gamma.data(), c, e, k_M, k_P, 0.0, 0.0};
+    // Ritz values of the filtered operator count as converged below this
+    // relative residual estimate; a float filter carries rounding noise of
+    // ~d * 6e-8 in every filtered vector, so it cannot go below ~1e-5.
+    const double conv_T = o->filter_prec == NM_F32 ? 1e-5 : 1e-8;
+
+    const int mmax = b * o->max_blocks;
+    const int ldv = mmax + b;
+    DevBuf V, W, MW, C, H, G, fin, fout;
+    NM_TRY(V.alloc((size_t)n * ldv * sizeof(double)));
+    NM_TRY(W.alloc((size_t)n * b * sizeof(double)));
+    NM_TRY(MW.alloc((size_t)n * b * sizeof(double)));
+    NM_TRY(C.alloc((size_t)ldv * b * sizeof(double)));
+    NM_TRY(H.alloc((size_t)ldv * b * sizeof(double)));
+    NM_TRY(G.alloc((size_t)b * b * sizeof(double)));
+    // start block
+    if (o->start) {
+        NM_TRY(launch_scale_copy<double>(n, b, 1.0, o->start, b, V.as<double>(), ldv, s));
+    } else {
+        NM_TRY(launch_philox_normal(n * b, o->seed, W.as<double>(), s));
+        NM_TRY(launch_scale_copy<double>(n, b, 1.0, W.as<double>(), b, V.as<double>(), ldv, s));
+    }
+    int ok = 1;
+    NM_TRY(m_orth(P, V.as<double>(), ldv, b, MW.as<double>(), G.as<double>(), &ok, s));
+    if (!ok) return fail(NM_ENOTCONV, "start block is rank deficient in the M inner product");
+    std::vector<double> Tfull((size_t)mmax * mmax, 0.0);
+    double t_filter = 0.0;
+    int blocks = 0;
+    RRResult rr;
+    bool converged = false;
+    int m_used = 0;
+    for (int j = 0; j < o->max_blocks; ++j) {
+        const int m = (j + 1) * b;   // basis columns including V_j
+        double* Vj = V.as<double>() + (int64_t)j * b;
+        NM_CUDA(cudaStreamSynchronize(s));
+        auto t0 = std::chrono::steady_clock::now();
+        NM_TRY(filter_block(P, &f, Vj, ldv, W.as<double>(), b, o->filter_prec, fin, fout, s));
+        NM_CUDA(cudaStreamSynchronize(s));
+        t_filter += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        // CGS2 against the whole basis in the M inner product
+        NM_CUDA(cudaMemsetAsync(H.p, 0, (size_t)m * b * sizeof(double), s));
+        for (int pass = 0; pass < 2; ++pass) {
+            NM_TRY(apply_M_pub<double>(P, W.as<double>(), b, MW.as<double>(), b, b, KRON_PLAIN, nullptr, s));
+            NM_TRY(gemm_VtW(ctx, n, m, b, V.as<double>(), ldv, MW.as<double>(), b, C.as<double>(), 0.0));
+            NM_TRY(gemm_WmVC(ctx, n, m, b, -1.0, V.as<double>(), ldv, C.as<double>(), m, W.as<double>(), b));
+            const double one = 1.0;
+            NM_CUBLAS(cublasDaxpy(ctx->cublas, m * b, &one, C.as<double>(), 1, H.as<double>(), 1));
+        }
+        std::vector<double> hH((size_t)m * b);
+        NM_CUDA(cudaMemcpyAsync(hH.data(), H.p, hH.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        // new block
+        double* Vn = V.as<double>() + (int64_t)(j + 1) * b;
+        NM_TRY(launch_scale_copy<double>(n, b, 1.0, W.as<double>(), b, Vn, ldv, s));
+        NM_TRY(m_orth(P, Vn, ldv, b, MW.as<double>(), G.as<double>(), &ok, s));
+        std::vector<double> hR((size_t)b * b);
+        NM_CUDA(cudaMemcpy(hR.data(), G.p, hR.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int cc = 0; cc < b; ++cc)
+            for (int r = 0; r < m; ++r) Tfull[(size_t)r + (size_t)(j * b + cc) * mmax] = hH[(size_t)r + (size_t)cc * m];
+        blocks = j + 1;
+        m_used = m;
+        // projected filtered operator: symmetrised T (m x m), eig on the device
+        std::vector<double> Tm((size_t)m * m);
+        for (int r = 0; r < m; ++r)
+            for (int cc = 0; cc < m; ++cc) {
+                const double a = r <= cc ? Tfull[(size_t)r + (size_t)cc * mmax] : Tfull[(size_t)cc + (size_t)r * mmax];
+                Tm[(size_t)r + (size_t)cc * m] = a;
+            }
+        DevBuf Td, wd;
+        NM_TRY(Td.alloc(Tm.size() * sizeof(double)));
+        NM_TRY(wd.alloc(m * sizeof(double)));
+        NM_CUDA(cudaMemcpy(Td.p, Tm.data(), Tm.size() * sizeof(double), cudaMemcpyHostToDevice));
+        NM_TRY(dense_eig(ctx, m, Td.as<double>(), nullptr, wd.as<double>()));
+        std::vector<double> th(m), Sv((size_t)m * m);
+        NM_CUDA(cudaMemcpy(th.data(), wd.p, m * sizeof(double), cudaMemcpyDeviceToHost));
+        NM_CUDA(cudaMemcpy(Sv.data(), Td.p, Sv.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        int nwanted = 0, nconv = 0;
+        for (int i = 0; i < m; ++i) {
+            if (th[i] < tau) continue;
+            ++nwanted;
+            // residual estimate || R_{j+1} S[last b rows, i] ||, R upper triangular (col-major)
+            double r2 = 0;
+            if (ok)
+                for (int r = 0; r < b; ++r) {
+                    double v = 0;
+                    for (int q = r; q < b; ++q) v += hR[(size_t)r + (size_t)q * b] * Sv[(size_t)(m - b + q) + (size_t)i * m];
+                    r2 += v * v;
+                }
+            if (std::sqrt(r2) <= conv_T * std::max(std::fabs(th[i]), 1.0)) ++nconv;
+        }
+        const bool last = j + 1 == o->max_blocks || !ok;
+        if ((nwanted > 0 && nconv == nwanted && (j + 1) % check == 0) || last) {
+            NM_TRY(rayleigh_ritz(P, V.as<double>(), ldv, m, lam_lo, lam_hi, nullptr, rr));
+            bool all = rr.k > 0;
+            for (double r : rr.res) all = all && r <= tol;
+            if (all || last) {
+                converged = all;
+                break;
+            }
+        }
+    }
+    nm_result* R = new (std::nothrow) nm_result();
+    if (!R) return fail(NM_ENOMEM, "host allocation failed");
+    int rc = rayleigh_ritz(P, V.as<double>(), ldv, m_used, lam_lo, lam_hi, &R->X, rr);
+    if (rc != NM_OK) {
+        delete R;
+        return rc;
+    }
+    R->lambda = rr.lam;
+    R->resid = rr.res;
+    R->info.k = rr.k;
+    R->info.n = n;
+    R->info.blocks = blocks;
+    R->info.m = m_used;
+    R->info.filter_applications = (int64_t)blocks * b;
+    R->info.lam_lo = blo;
+    R->info.lam_hi = bhi;
+    R->info.seconds_filter = t_filter;
+    R->info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    *out = R;
+    bool all = rr.k > 0;
+    for (double r : rr.res) all = all && r <= tol;
+    if (!converged && !all) return fail(NM_ENOTCONV, "slice did not converge within max_blocks");
+    return NM_OK;
+}
+
+// ------------------------------------------------------------------ Ritz entry
+__global__ void interleave_complex_kernel(int64_t count, const double* re, const double* im, double* out) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        out[2 * t] = re[t];
+        out[2 * t + 1] = im[t];
+    }
+}
+
+int ritz(nm_problem* P, nm_ritz_mode mode, const double* V, int64_t ldv, int m, const double* lam_e,
+         nm_result** out) {
+    auto t_start = std::chrono::steady_clock::now();
+    nm_ctx* ctx = P->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t n = P->info.n;
+    if (m < 1 || !V || ldv < m) return fail(NM_EINVAL, "ritz needs m >= 1, V and ldv >= m");
+    if (!P->have_interval) return fail(NM_EINVAL, "call nm_set_interval first");
+    nm_result* R = new (std::nothrow) nm_result();
+    if (!R) return fail(NM_ENOMEM, "host allocation failed");
+    std::unique_ptr<nm_result> guard(R);
+    if (mode == NM_RITZ_PENCIL) {
+        const double lam_lo = P->lo <= 0 ? -1e-8 * std::max(1.0, std::fabs(P->hi)) : P->lo;
+        RRResult rr;
+        NM_TRY(rayleigh_ritz(P, V, ldv, m, lam_lo, P->hi, &R->X, rr));
+        R->lambda = rr.lam;
+        R->resid = rr.res;
+        R->info.k = rr.k;
+        R->info.n = n;
+        R->info.m = m;
+    } else if (mode == NM_RITZ_ROTATING) {
+        if (!lam_e) return fail(NM_EINVAL, "rotating mode needs the Ritz values lam_e");
+        for (int i = 0; i < m; ++i)
+            if (!(lam_e[i] > 0)) return fail(NM_EINVAL, "rotating mode needs lam_e > 0");
+        // Q = X^T R X (real skew), R X = (M_rho (x) [Omega]_x) X
+        DevBuf RX, Q;
+        NM_TRY(RX.alloc((size_t)n * m * sizeof(double)));
+        NM_TRY(Q.alloc((size_t)m * m * sizeof(double)));
+        NM_TRY(apply_cols(P, 2, V, ldv, RX.as<double>(), m, m, 0, s));
+        NM_TRY(gemm_VtW(ctx, n, m, m, V, ldv, RX.as<double>(), m, Q.as<double>(), 0.0));
+        std::vector<double> hQ((size_t)m * m);
+        NM_CUDA(cudaMemcpyAsync(hQ.data(), Q.p, hQ.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        NM_CUDA(cudaStreamSynchronize(s));
+        // pencil [[0, L], [L, 2iQ]] y = w [[L, 0], [0, I]] y (eq. sublinear0), complex Hermitian
+        const int m2 = 2 * m;
+        std::vector<cuDoubleComplex> A((size_t)m2 * m2, make_cuDoubleComplex(0, 0)), B(A);
+        for (int i = 0; i < m; ++i) {
+            A[(size_t)i + (size_t)(m + i) * m2] = make_cuDoubleComplex(lam_e[i], 0);
+            A[(size_t)(m + i) + (size_t)i * m2] = make_cuDoubleComplex(lam_e[i], 0);
+            B[(size_t)i + (size_t)i * m2] = make_cuDoubleComplex(lam_e[i], 0);
+            B[(size_t)(m + i) + (size_t)(m + i) * m2] = make_cuDoubleComplex(1, 0);
+        }
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                // Hermitian part of 2iQ: Q skew => 2iQ Hermitian; symmetrise against rounding
+                const double q = 0.5 * (hQ[(size_t)i + (size_t)j * m] - hQ[(size_t)j + (size_t)i * m]);
+                A[(size_t)(m + i) + (size_t)(m + j) * m2] = make_cuDoubleComplex(0, 2.0 * q);
+            }
+        DevBuf Ad, Bd, wd, info;
+        NM_TRY(Ad.alloc(A.size() * sizeof(cuDoubleComplex)));
+        NM_TRY(Bd.alloc(B.size() * sizeof(cuDoubleComplex)));
+        NM_TRY(wd.alloc(m2 * sizeof(double)));
+        NM_TRY(info.alloc(sizeof(int)));
+        NM_CUDA(cudaMemcpy(Ad.p, A.data(), A.size() * sizeof(cuDoubleComplex), cudaMemcpyHostToDevice));
+        NM_CUDA(cudaMemcpy(Bd.p, B.data(), B.size() * sizeof(cuDoubleComplex), cudaMemcpyHostToDevice));
+        int lwork = 0;
+        NM_CUSOLVER(cusolverDnZhegvd_bufferSize(ctx->cusolver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                                                CUBLAS_FILL_MODE_UPPER, m2, Ad.as<cuDoubleComplex>(), m2,
+                                                Bd.as<cuDoubleComplex>(), m2, wd.as<double>(), &lwork));
+        DevBuf work;
+        NM_TRY(work.alloc(std::max(lwork, 1) * sizeof(cuDoubleComplex)));
+        NM_CUSOLVER(cusolverDnZhegvd(ctx->cusolver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                                     CUBLAS_FILL_MODE_UPPER, m2, Ad.as<cuDoubleComplex>(), m2,
+                                     Bd.as<cuDoubleComplex>(), m2, wd.as<double>(), work.as<cuDoubleComplex>(),
+                                     lwork, info.as<int>()));
+        int h = 0;
+        NM_CUDA(cudaMemcpy(&h, info.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (h != 0) return fail(NM_ENOTCONV, "rotating dense eigensolver failed");
+        std::vector<double> w(m2);
+        std::vector<cuDoubleComplex> Y((size_t)m2 * m2);
+        NM_CUDA(cudaMemcpy(w.data(), wd.p, m2 * sizeof(double), cudaMemcpyDeviceToHost));
+        NM_CUDA(cudaMemcpy(Y.data(), Ad.p, Y.size() * sizeof(cuDoubleComplex), cudaMemcpyDeviceToHost));
+        const double wlo = P->lo > 0 ? std::sqrt(P->lo) : 0.0, whi = std::sqrt(std::max(P->hi, 0.0));
+        std::vector<int> sel;
+        for (int i = 0; i < m2; ++i)
+            if (w[i] >= wlo && w[i] <= whi) sel.push_back(i);
+        const int k = (int)sel.size();
+        R->lambda.resize(k);
+        R->resid.assign(k, 0.0);
+        R->info.k = k;
+        R->info.n = n;
+        R->info.m = m;
+        R->info.complex_vectors = 1;
+        if (k > 0) {
+            // y_top (m x k) real and imaginary parts, col-major; u = X_e y_top
+            std::vector<double> yr((size_t)m * k), yi((size_t)m * k);
+            for (int c = 0; c < k; ++c) {
+                R->lambda[c] = w[sel[c]];
+                for (int i = 0; i < m; ++i) {
+                    yr[(size_t)i + (size_t)c * m] = cuCreal(Y[(size_t)i + (size_t)sel[c] * m2]);
+                    yi[(size_t)i + (size_t)c * m] = cuCimag(Y[(size_t)i + (size_t)sel[c] * m2]);
+                }
+            }
+            DevBuf yrd, yid, Ur, Ui;
+            NM_TRY(yrd.alloc(yr.size() * sizeof(double)));
+            NM_TRY(yid.alloc(yi.size() * sizeof(double)));
+            NM_TRY(Ur.alloc((size_t)n * k * sizeof(double)));
+            NM_TRY(Ui.alloc((size_t)n * k * sizeof(double)));
+            NM_CUDA(cudaMemcpy(yrd.p, yr.data(), yr.size() * sizeof(double), cudaMemcpyHostToDevice));
+            NM_CUDA(cudaMemcpy(yid.p, yi.data(), yi.size() * sizeof(double), cudaMemcpyHostToDevice));
+            const double one = 1.0, zero = 0.0;
+            NM_CUBLAS(cublasDgemm(ctx->cublas, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)n, m, &one, yrd.as<double>(), m, V,
+                                  (int)ldv, &zero, Ur.as<double>(), k));
+            NM_CUBLAS(cublasDgemm(ctx->cublas, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)n, m, &one, yid.as<double>(), m, V,
+                                  (int)ldv, &zero, Ui.as<double>(), k));
+            // full quadratic residual ||w^2 M u - 2 i w R u - K u|| / ||w^2 M u|| (reported, not gated)
+            DevBuf KUr, KUi, MUr, MUi, RUr, RUi;
+            for (DevBuf* d : {&KUr, &KUi, &MUr, &MUi, &RUr, &RUi}) NM_TRY(d->alloc((size_t)n * k * sizeof(double)));
+            NM_TRY(apply_cols(P, 0, Ur.as<double>(), k, KUr.as<double>(), k, k, 80, s));
+            NM_TRY(apply_cols(P, 0, Ui.as<double>(), k, KUi.as<double>(), k, k, 80, s));
+            NM_TRY(apply_cols(P, 1, Ur.as<double>(), k, MUr.as<double>(), k, k, 0, s));
+            NM_TRY(apply_cols(P, 1, Ui.as<double>(), k, MUi.as<double>(), k, k, 0, s));
+            NM_TRY(apply_cols(P, 2, Ur.as<double>(), k, RUr.as<double>(), k, k, 0, s));
+            NM_TRY(apply_cols(P, 2, Ui.as<double>(), k, RUi.as<double>(), k, k, 0, s));
+            std::vector<double> hK[2], hM[2], hRr[2];
+            for (int p = 0; p < 2; ++p) {
+                hK[p].resize((size_t)n * k);
+                hM[p].resize((size_t)n * k);
+                hRr[p].resize((size_t)n * k);
+            }
+            NM_CUDA(cudaMemcpy(hK[0].data(), KUr.p, (size_t)n * k * 8, cudaMemcpyDeviceToHost));
+            NM_CUDA(cudaMemcpy(hK[1].data(), KUi.p, (size_t)n * k * 8, cudaMemcpyDeviceToHost));
+            NM_CUDA(cudaMemcpy(hM[0].data(), MUr.p, (size_t)n * k * 8, cudaMemcpyDeviceToHost));
+            NM_CUDA(cudaMemcpy(hM[1].data(), MUi.p, (size_t)n * k * 8, cudaMemcpyDeviceToHost));
+            NM_CUDA(cudaMemcpy(hRr[0].data(), RUr.p, (size_t)n * k * 8, cudaMemcpyDeviceToHost));
+            NM_CUDA(cudaMemcpy(hRr[1].data(), RUi.p, (size_t)n * k * 8, cudaMemcpyDeviceToHost));
+            for (int c = 0; c < k; ++c) {
+                const double om = R->lambda[c];
+                double num = 0, den = 0;
+                for (int64_t i = 0; i < n; ++i) {
+                    const size_t q = (size_t)i * k + c;
+                    // w^2 M u - 2 i w R u - K u
+                    const double re = om * om * hM[0][q] + 2 * om * hRr[1][q] - hK[0][q];
+                    const double im = om * om * hM[1][q] - 2 * om * hRr[0][q] - hK[1][q];
+                    num += re * re + im * im;
+                    den += om * om * om * om * (hM[0][q] * hM[0][q] + hM[1][q] * hM[1][q]);
+                }
+                R->resid[c] = den > 0 ? std::sqrt(num / den) : 0.0;
+            }
+            NM_TRY(R->X.alloc((size_t)n * k * 2 * sizeof(double)));
+            interleave_complex_kernel<<<(unsigned)std::min<int64_t>((n * k + 255) / 256, 4864), 256, 0, s>>>(
+                n * k, Ur.as<double>(), Ui.as<double>(), R->X.as<double>());
+            count_launch();
+        NM_CUDA(cudaGetLastError());
+            NM_CUDA(cudaStreamSynchronize(s));
+        }
+    } else {
+        return fail(NM_EINVAL, "unknown ritz mode");
+    }
+    R->info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    *out = guard.release();
+    return NM_OK;
+}
+
+}  // namespace nm

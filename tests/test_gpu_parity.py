@@ -1,0 +1,299 @@
+"""GPU (libnm, through the C ABI) against the CPU oracle, element by element.
+
+Sizes: the ~400-tet homogeneous ball and a coarse three-layer planet with a
+fluid core and reference gravity, small enough for dense oracle solves yet
+spanning many thread blocks, with ragged block widths (1, 5, 33, 64) and
+leading dimensions larger than the width.
+
+Tolerances (derived from the arithmetic): assembled FP64 values differ
+only by summation order (atomics vs sorted COO): 1e-12 relative to the
+largest entry. One FP64 SpMM / mass-solve / filter: 1e-12 .. 1e-9
+relative (the filter runs d x k_M dependent steps). FP32 kernels: 2e-5
+relative for one product (z ~ 30-60 terms of 6e-8 each), 1e-3 relative
+for a whole FP32 filter application. Eigenvalues: 1e-8 relative (1e-10
+lambda_max absolute for the rigid-body zero modes), residuals <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from synth.model import config_ball, layered_planet  # noqa: E402
+from oracle import fem, eig, filtlan  # noqa: E402
+from tests.helpers import gpu_csr_to_canonical, to_internal, to_canonical, rel_err  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def nm():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1906_11082_gb300 import nm as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def ctx(nm):
+    return nm.Context(0)
+
+
+@pytest.fixture(scope="module")
+def ball(nm, ctx):
+    w = config_ball()
+    S = fem.assemble(w.mesh, w.model)
+    P = nm.Problem(ctx, w.mesh, w.model)
+    return w, S, P
+
+
+@pytest.fixture(scope="module")
+def planet(nm, ctx):
+    mesh, model = layered_planet(h=0.25, seed=7)
+    S = fem.assemble(mesh, model)
+    P = nm.Problem(ctx, mesh, model)
+    return mesh, model, S, P
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.tensor(a, dtype=dtype, device=DEV)
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+# ------------------------------------------------------------------ assembly
+def test_ball_assembly_matches_oracle(ball):
+    w, S, P = ball
+    assert P.n == S.n and P.info["Np"] == 0
+    AG = gpu_csr_to_canonical(P, 0)
+    Mr = gpu_csr_to_canonical(P, 1)
+    assert rel_err(AG.toarray(), S.A_G.toarray()) <= 1e-12
+    assert rel_err(Mr.toarray(), S.M_rho.toarray()) <= 1e-12
+
+
+def test_planet_assembly_matches_oracle(planet):
+    mesh, model, S, P = planet
+    assert P.n == S.n and P.Np == S.dm.Np and P.info["n_fs"] > 0
+    canon, p2, _ = P.unodes()
+    g = P.gravity()
+    g_or = S.g_p2[p2]
+    assert rel_err(g, g_or) <= 1e-12
+    assert rel_err(gpu_csr_to_canonical(P, 0).toarray(), S.A_G.toarray()) <= 1e-12
+    assert rel_err(gpu_csr_to_canonical(P, 1).toarray(), S.M_rho.toarray()) <= 1e-12
+    assert rel_err(gpu_csr_to_canonical(P, 2).toarray(), (-S.A_p).toarray()) <= 1e-12
+    assert rel_err(gpu_csr_to_canonical(P, 3).toarray(), S.E_G.toarray()) <= 1e-12
+    assert rel_err(gpu_csr_to_canonical(P, 4).toarray(), S.E_G.T.toarray()) <= 1e-12
+
+
+def test_supplied_gprime_is_used(nm, ctx, planet):
+    mesh, model, S, _ = planet
+    gp = S.g_p2 * 1.1
+    P2 = nm.Problem(ctx, mesh, model, gprime=gp)
+    _, p2, _ = P2.unodes()
+    assert rel_err(P2.gravity(), gp[p2]) <= 1e-15
+
+
+# ------------------------------------------------------------------ operator pieces
+@pytest.mark.parametrize("b,ld", [(1, 1), (5, 7), (33, 33), (64, 70)])
+def test_apply_K_M_R_match_oracle(planet, b, ld):
+    mesh, model, S, P = planet
+    rng = np.random.default_rng(b)
+    Xc = rng.standard_normal((S.n, b))
+    X = torch.zeros((S.n, ld), dtype=torch.float64, device=DEV)
+    X[:, :b] = _dev(to_internal(P, Xc))
+    Y = torch.zeros_like(X)
+    op = filtlan.Operator(S, k_M=10, k_P=80)
+    P.apply_K(X[:, :b], Y[:, :b], k_P=80)
+    ref = op.K(Xc)
+    assert rel_err(to_canonical(P, _host(Y[:, :b])), ref) <= 1e-11
+    P.apply_M(X[:, :b], Y[:, :b])
+    assert rel_err(to_canonical(P, _host(Y[:, :b])), S.M @ Xc) <= 1e-12
+    # ld padding untouched
+    assert torch.count_nonzero(Y[:, b:]).item() == 0
+
+
+def test_apply_R_matches_oracle(nm, ctx):
+    mesh, model = layered_planet(h=0.25, seed=7, omega=0.3)
+    S = fem.assemble(mesh, model)
+    P = nm.Problem(ctx, mesh, model)
+    Xc = np.random.default_rng(0).standard_normal((S.n, 4))
+    Y = torch.empty((S.n, 4), dtype=torch.float64, device=DEV)
+    P.apply_R(_dev(to_internal(P, Xc)), Y)
+    assert rel_err(to_canonical(P, _host(Y)), S.R @ Xc) <= 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2, 7, 40])
+def test_solve_M_matches_oracle(planet, k):
+    mesh, model, S, P = planet
+    Wc = np.random.default_rng(k).standard_normal((S.n, 3))
+    X = torch.empty((S.n, 3), dtype=torch.float64, device=DEV)
+    P.solve_M(_dev(to_internal(P, Wc)), X, k_M=k)
+    ref = filtlan.cheb_solve(S.M, 1.0 / S.M.diagonal(), Wc, k)
+    assert rel_err(to_canonical(P, _host(X)), ref) <= 1e-12
+
+
+def test_fp32_pieces(planet):
+    mesh, model, S, P = planet
+    Xc = np.random.default_rng(3).standard_normal((S.n, 8))
+    X = _dev(to_internal(P, Xc), torch.float32)
+    Y = torch.empty_like(X)
+    P.apply_M(X, Y)
+    assert rel_err(to_canonical(P, _host(Y)), S.M @ Xc) <= 2e-5
+    P.apply_K(X, Y, k_P=40)
+    op = filtlan.Operator(S, k_M=10, k_P=40)
+    assert rel_err(to_canonical(P, _host(Y)), op.K(Xc)) <= 1e-4
+
+
+# ------------------------------------------------------------------ filter
+@pytest.mark.parametrize("which,d,kM,b", [("ball", 30, 12, 8), ("ball", 1, 2, 3), ("planet", 12, 8, 5)])
+def test_filter_apply_fp64(ball, planet, nm, which, d, kM, b):
+    S, P = (ball[1], ball[2]) if which == "ball" else (planet[2], planet[3])
+    op = filtlan.Operator(S, k_M=kM, k_P=kM)
+    lo, hi = filtlan.spectrum_bounds(op, S.n)
+    gam, c, e = filtlan.filter_coeffs(lo, hi, 0.5, 9.0, d)
+    Yc = np.random.default_rng(d).standard_normal((S.n, b))
+    Z = torch.empty((S.n, b), dtype=torch.float64, device=DEV)
+    P.filter_apply(gam, c, e, kM, _dev(to_internal(P, Yc)), Z, k_P=kM)
+    ref = filtlan.filter_apply(op, gam, c, e, Yc)
+    assert rel_err(to_canonical(P, _host(Z)), ref) <= 1e-9
+
+
+def test_filter_apply_fp32(ball):
+    _, S, P = ball
+    op = filtlan.Operator(S, k_M=12)
+    gam, c, e = filtlan.filter_coeffs(-1.0, 5000.0, 0.0, 9.0, 30)
+    Yc = np.random.default_rng(0).standard_normal((S.n, 16))
+    Z = torch.empty((S.n, 16), dtype=torch.float32, device=DEV)
+    P.filter_apply(gam, c, e, 12, _dev(to_internal(P, Yc), torch.float32), Z)
+    ref = filtlan.filter_apply(op, gam, c, e, Yc)
+    assert rel_err(to_canonical(P, _host(Z)), ref) <= 1e-3
+
+
+# ------------------------------------------------------------------ bounds and slices
+def test_spectrum_bounds_enclose(ball):
+    w, S, P = ball
+    lo, hi = P.spectrum_bounds(steps=40, k_M=40)
+    K, M = eig.pencil_dense(S)
+    lam = eig.all_eigs(K, M)[0]
+    assert lo <= lam[0] and hi >= lam[-1] and hi <= 1.2 * lam[-1]
+
+
+def _check_slice(res, ref, lam_max):
+    assert len(res.lam) == len(ref)
+    big = np.abs(ref) > 1e-10 * lam_max
+    assert np.allclose(res.lam[big], ref[big], rtol=1e-8)
+    if (~big).any():
+        assert np.abs(res.lam[~big]).max() <= 1e-10 * lam_max
+    assert res.resid.max() <= 1e-6
+
+
+def test_lanczos_slice_ball_fp64(ball):
+    w, S, P = ball
+    P.set_interval(0.0, 3.0)
+    res = P.lanczos_slice(block=8, degree=100, k_M=40, k_P=40, max_blocks=16, seed=5)
+    K, M = eig.pencil_dense(S)
+    lam, Xd = eig.all_eigs(K, M)
+    ref = lam[(lam >= -1e-8 * lam[-1]) & (lam <= 9.0)]
+    _check_slice(res, ref, lam[-1])
+    # eigenspace: the computed vectors lie in the span of the reference ones
+    X = to_canonical(P, _host(res.vectors()))
+    sel = (lam >= -1e-8 * lam[-1]) & (lam <= 9.0)
+    Q = Xd[:, sel]
+    proj = X - Q @ (Q.T @ (M @ X))
+    assert np.linalg.norm(proj) <= 1e-6 * np.linalg.norm(X)
+    # M-orthonormal
+    G = X.T @ (M @ X)
+    assert np.abs(G - np.eye(len(res.lam))).max() <= 1e-8
+
+
+def test_lanczos_slice_ball_fp32_filter(nm, ball):
+    """A float filter leaves white rounding noise (~d x 6e-8) in the basis;
+    the exact-pencil residual amplifies it by lambda_max / lambda, so only
+    the eigenvalues (second order in the vector error) reach FP64 accuracy."""
+    w, S, P = ball
+    P.set_interval(0.0, 3.0)
+    res = P.lanczos_slice(block=8, degree=100, k_M=28, k_P=28, max_blocks=16, seed=6, prec=nm.NM_F32,
+                          tol=1e-2)
+    K, M = eig.pencil_dense(S)
+    lam = eig.all_eigs(K, M)[0]
+    ref = lam[(lam >= -1e-8 * lam[-1]) & (lam <= 9.0)]
+    assert len(res.lam) == len(ref)
+    big = np.abs(ref) > 1e-10 * lam[-1]
+    assert np.allclose(res.lam[big], ref[big], rtol=1e-6)
+    assert res.resid.max() <= 1e-2
+
+
+def test_lanczos_slice_ball_mixed(nm, ball):
+    w, S, P = ball
+    P.set_interval(0.0, 3.0)
+    res = P.lanczos_slice(block=8, degree=100, k_M=28, k_P=28, max_blocks=16, seed=7, prec=nm.NM_MIXED)
+    K, M = eig.pencil_dense(S)
+    lam = eig.all_eigs(K, M)[0]
+    ref = lam[(lam >= -1e-8 * lam[-1]) & (lam <= 9.0)]
+    _check_slice(res, ref, lam[-1])
+
+
+@pytest.mark.parametrize("k", [7, 28])
+def test_solve_M_mixed_matches_refined_oracle(nm, planet, k):
+    mesh, model, S, P = planet
+    Wc = np.random.default_rng(k).standard_normal((S.n, 6))
+    X = torch.empty((S.n, 6), dtype=torch.float64, device=DEV)
+    P.solve_M(_dev(to_internal(P, Wc)), X, k_M=k, prec=nm.NM_MIXED)
+    ref = filtlan.refined_solve(S.M, 1.0 / S.M.diagonal(), Wc, k)
+    # float semi-iterations add ~6e-8 x |residual| of noise
+    tol = 1e-11 if k == 28 else 1e-8
+    assert rel_err(to_canonical(P, _host(X)), ref) <= tol
+
+
+def test_apply_K_mixed_matches_refined_oracle(nm, planet):
+    mesh, model, S, P = planet
+    Xc = np.random.default_rng(9).standard_normal((S.n, 4))
+    Y = torch.empty((S.n, 4), dtype=torch.float64, device=DEV)
+    P.apply_K(_dev(to_internal(P, Xc)), Y, k_P=28, prec=nm.NM_MIXED)
+    op = filtlan.Operator(S, k_M=28, k_P=28, refine=True)
+    assert rel_err(to_canonical(P, _host(Y)), op.K(Xc)) <= 1e-11
+
+
+def test_filter_apply_mixed(nm, planet):
+    mesh, model, S, P = planet
+    op = filtlan.Operator(S, k_M=20, k_P=20, refine=True)
+    lo, hi = filtlan.spectrum_bounds(op, S.n)
+    gam, c, e = filtlan.filter_coeffs(lo, hi, 0.5, 9.0, 20)
+    Yc = np.random.default_rng(4).standard_normal((S.n, 8))
+    Z = torch.empty((S.n, 8), dtype=torch.float64, device=DEV)
+    P.filter_apply(gam, c, e, 20, _dev(to_internal(P, Yc)), Z, k_P=20, prec=nm.NM_MIXED)
+    ref = filtlan.filter_apply(op, gam, c, e, Yc)
+    assert rel_err(to_canonical(P, _host(Z)), ref) <= 1e-8
+
+
+def test_lanczos_slice_planet(planet):
+    mesh, model, S, P = planet
+    K, M = eig.pencil_dense(S)
+    lam = eig.all_eigs(K, M)[0]
+    # a slice of seismic modes well above the fluid band, edges in spectral gaps
+    hi_sel = lam[lam > 0.5]
+    lo_edge = 0.5 * (hi_sel[3] + hi_sel[4])
+    hi_edge = 0.5 * (hi_sel[15] + hi_sel[16])
+    P.set_interval(lo_edge, hi_edge, unit=1)
+    res = P.lanczos_slice(block=8, degree=80, k_M=40, k_P=40, max_blocks=30, seed=2)
+    ref = lam[(lam >= lo_edge) & (lam <= hi_edge)]
+    _check_slice(res, ref, lam[-1])
+
+
+def test_empty_slice_reports_not_converged(nm, ball):
+    w, S, P = ball
+    P.set_interval(3.05, 3.1)   # gap between 0S2 and 1S1 on this mesh
+    res = P.lanczos_slice(block=4, degree=40, k_M=20, k_P=20, max_blocks=3, seed=1, allow_unconverged=True)
+    assert len(res.lam) == 0
+
+
+def test_invalid_block_width(nm, ball):
+    _, S, P = ball
+    X = torch.zeros((S.n, 65), dtype=torch.float64, device=DEV)
+    with pytest.raises(nm.NMError) as e:
+        P.apply_M(X, X.clone())
+    assert e.value.code == nm.NM_EINVAL
