@@ -527,6 +527,46 @@ static int upload_pattern(DevCSR& A, int64_t nrows, int64_t ncols, int rb, int c
     return NM_OK;
 }
 
+// Row tiles of a scalar square pattern (see DevCSR): the distinct columns of
+// each tile of `rows` consecutive rows and every entry's local position.
+static int build_tiles(DevCSR& A, int rows) {
+    const int64_t n = A.nrows;
+    A.tile_rows = rows;
+    A.ntiles = (n + rows - 1) / rows;
+    std::vector<int32_t> uptr(A.ntiles + 1, 0), ucol;
+    std::vector<uint16_t> lcol(std::max<int64_t>(A.nnz, 1));
+    ucol.reserve((size_t)n * 6);
+    int umax = 0;
+    std::vector<int32_t> tmp;
+    for (int64_t t = 0; t < A.ntiles; ++t) {
+        const int64_t r0 = t * rows, r1 = std::min<int64_t>(n, r0 + rows);
+        tmp.assign(A.h_col.begin() + A.h_rowptr[r0], A.h_col.begin() + A.h_rowptr[r1]);
+        std::sort(tmp.begin(), tmp.end());
+        tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+        if (tmp.size() > 65535) return fail(NM_EUNSUPPORTED, "tile with more than 65535 distinct columns");
+        umax = std::max<int>(umax, (int)tmp.size());
+        for (int64_t e = A.h_rowptr[r0]; e < A.h_rowptr[r1]; ++e)
+            lcol[e] = (uint16_t)(std::lower_bound(tmp.begin(), tmp.end(), A.h_col[e]) - tmp.begin());
+        ucol.insert(ucol.end(), tmp.begin(), tmp.end());
+        uptr[t + 1] = (int32_t)ucol.size();
+    }
+    A.tile_umax = umax;
+    NM_TRY(upload(A.tile_uptr, uptr));
+    NM_TRY(upload(A.tile_ucol, ucol));
+    NM_TRY(upload(A.lcol, lcol));
+    return NM_OK;
+}
+
+// Largest tile height (power of two, <= 64) whose staged float operand of
+// b = 32 columns and R sub-rows fits `budget` bytes of shared memory.
+static int pick_tiles(DevCSR& A, int R, size_t budget) {
+    for (int rows = 64; rows >= 4; rows /= 2) {
+        NM_TRY(build_tiles(A, rows));
+        if ((size_t)A.tile_umax * R * 32 * sizeof(float) <= budget) return NM_OK;
+    }
+    return NM_OK;
+}
+
 // ------------------------------------------------------------ nm_assemble
 int assemble(nm_ctx* ctx, const nm_mesh* mesh, const nm_model* mdl, nm_problem* P) {
     const int64_t nv = mesh->nv, nt = mesh->nt;
@@ -893,6 +933,8 @@ int assemble(nm_ctx* ctx, const nm_mesh* mesh, const nm_model* mdl, nm_problem* 
     NM_CUDA(cudaStreamSynchronize(s));
     NM_TRY(make_dinv(P->Mr));
     if (Np > 0) NM_TRY(make_dinv(P->Pn));
+    NM_TRY(pick_tiles(P->Mr, 3, 100 * 1024));
+    if (Np > 0) NM_TRY(pick_tiles(P->Pn, 1, 100 * 1024));
     NM_CUDA(cudaStreamSynchronize(s));
 
     auto& I = P->info;

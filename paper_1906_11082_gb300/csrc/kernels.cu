@@ -33,6 +33,43 @@ static inline int tpr_shift_for(int b) {
 constexpr int kThreads = 256;
 
 // ----------------------------------------------------------------- A (x) I_R
+// Output stage shared by the plain and the tiled kernels: acc holds
+// (A (x) I_R) x_k for node `row`, column c.
+template <typename T, int R, int MODE>
+__device__ __forceinline__ void kron_epilogue(const KronArgs<T>& a, int64_t row, int c, const T* acc) {
+    if (MODE == KRON_PLAIN) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) a.Y[(R * row + k) * a.ldy + c] = acc[k];
+    } else if (MODE == KRON_CORI) {
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            T y = T(0);
+#pragma unroll
+            for (int k = 0; k < R; ++k) y += a.sk[m * 3 + k] * acc[k];
+            a.Y[(R * row + m) * a.ldy + c] = y;
+        }
+    } else {
+        const T d = a.dinv[row] * a.inv_theta;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int64_t r = R * row + k;
+            const T xk = a.X[r * a.ldx + c];
+            const T w = a.W[r * a.ldw + c];
+            const T xp = a.Xp ? a.Xp[r * a.ldp + c] : T(0);
+            const T xn = xp + a.om * (xk - xp + d * (w - acc[k]));
+            if (MODE == KRON_CHEB) {
+                a.Xn[r * a.ldn + c] = xn;
+            } else {
+                const T tk = a.Tk[r * a.ldtk + c];
+                const T tp = a.Tp ? a.Tp[r * a.ldtp + c] : T(0);
+                const T tn = a.a1 * (xn - a.cshift * tk) - a.a2 * tp;
+                a.Tn[r * a.ldtn + c] = tn;
+                if (a.Z) a.Z[r * a.ldz + c] += a.gam * tn;
+            }
+        }
+    }
+}
+
 template <typename T, int R, int CPT, int MODE>
 __global__ void __launch_bounds__(kThreads) kron_kernel(const KronArgs<T> a, int tpr_shift) {
     const int tpr = 1 << tpr_shift;
@@ -62,37 +99,7 @@ __global__ void __launch_bounds__(kThreads) kron_kernel(const KronArgs<T> a, int
     for (int q = 0; q < CPT; ++q) {
         const int c = lane + q * tpr;
         if (c >= a.b) continue;
-        if (MODE == KRON_PLAIN) {
-#pragma unroll
-            for (int k = 0; k < R; ++k) a.Y[(R * row + k) * a.ldy + c] = acc[q][k];
-        } else if (MODE == KRON_CORI) {
-#pragma unroll
-            for (int m = 0; m < R; ++m) {
-                T y = T(0);
-#pragma unroll
-                for (int k = 0; k < R; ++k) y += a.sk[m * 3 + k] * acc[q][k];
-                a.Y[(R * row + m) * a.ldy + c] = y;
-            }
-        } else {
-            const T d = a.dinv[row] * a.inv_theta;
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                const int64_t r = R * row + k;
-                const T xk = a.X[r * a.ldx + c];
-                const T w = a.W[r * a.ldw + c];
-                const T xp = a.Xp ? a.Xp[r * a.ldp + c] : T(0);
-                const T xn = xp + a.om * (xk - xp + d * (w - acc[q][k]));
-                if (MODE == KRON_CHEB) {
-                    a.Xn[r * a.ldn + c] = xn;
-                } else {
-                    const T tk = a.Tk[r * a.ldtk + c];
-                    const T tp = a.Tp ? a.Tp[r * a.ldtp + c] : T(0);
-                    const T tn = a.a1 * (xn - a.cshift * tk) - a.a2 * tp;
-                    a.Tn[r * a.ldtn + c] = tn;
-                    if (a.Z) a.Z[r * a.ldz + c] += a.gam * tn;
-                }
-            }
-        }
+        kron_epilogue<T, R, MODE>(a, row, c, acc[q]);
     }
 }
 
@@ -110,9 +117,90 @@ static int kron_dispatch_cpt(int cpt, const KronArgs<T>& a, int shift, cudaStrea
     return NM_OK;
 }
 
+// Tiled variant for float blocks of exactly 32 columns (ld 32): one CTA per
+// tile of consecutive rows. The tile's distinct neighbour nodes (R x 32
+// floats each, 16-byte aligned runs) are copied into shared memory with
+// cp.async; each warp then owns rows of the tile, lane = column, and reads
+// its 32 (value, local column) pairs per round with one coalesced load plus
+// warp shuffles.
+template <int R, int MODE>
+__global__ void __launch_bounds__(kThreads) kron_tile_kernel(const KronArgs<float> a) {
+    extern __shared__ float4 kron_smem4[];
+    float* xs = reinterpret_cast<float*>(kron_smem4);
+    constexpr int RB = R * 32;          // floats per staged node
+    constexpr int PER = RB / 4;         // 16-byte chunks per staged node
+    const int64_t t = blockIdx.x;
+    const int u0 = __ldg(a.tile_uptr + t);
+    const int U = __ldg(a.tile_uptr + t + 1) - u0;
+    for (int i = threadIdx.x; i < U * PER; i += kThreads) {
+        const int u = i / PER, q = i - u * PER;
+        const int64_t node = __ldg(a.tile_ucol + u0 + u);
+        const int k = (4 * q) >> 5, cc = (4 * q) & 31;
+        const float* src = a.X + ((int64_t)R * node + k) * 32 + cc;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(xs + u * RB + 4 * q);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int rr = warp; rr < a.tile_rows; rr += kThreads / 32) {
+        const int64_t row = t * a.tile_rows + rr;
+        if (row >= a.nrows) break;
+        float acc[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[k] = 0.f;
+        const int e0 = __ldg(a.rowptr + row), e1 = __ldg(a.rowptr + row + 1);
+        for (int base = e0; base < e1; base += 32) {
+            const int e = base + lane;
+            const float vr = e < e1 ? __ldg(a.val + e) : 0.f;
+            const int lr = e < e1 ? (int)__ldg(a.lcol + e) : 0;
+            const int cnt = min(32, e1 - base);
+            for (int j = 0; j < cnt; ++j) {
+                const float v = __shfl_sync(0xffffffffu, vr, j);
+                const int l = __shfl_sync(0xffffffffu, lr, j);
+                const float* xr = xs + l * RB;
+#pragma unroll
+                for (int k = 0; k < R; ++k) acc[k] += v * xr[k * 32 + lane];
+            }
+        }
+        kron_epilogue<float, R, MODE>(a, row, lane, acc);
+    }
+}
+
+template <int R, int MODE>
+static int kron_tile_launch(const KronArgs<float>& a, cudaStream_t s) {
+    const size_t smem = (size_t)a.tile_umax * R * 32 * sizeof(float);
+    static bool attr_set = false;
+    if (!attr_set) {
+        NM_CUDA(cudaFuncSetAttribute(kron_tile_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     200 * 1024));
+        attr_set = true;
+    }
+    kron_tile_kernel<R, MODE><<<(unsigned)a.ntiles, kThreads, smem, s>>>(a);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+template <typename T>
+static bool tiled_ok(const KronArgs<T>& a) {
+    if (!std::is_same<T, float>::value || !a.tile_uptr || a.b != 32 || a.ldx != 32) return false;
+    if (((uintptr_t)a.X & 15) != 0) return false;
+    return (size_t)a.tile_umax * 3 * 32 * sizeof(float) <= 200 * 1024;
+}
+
 template <typename T>
 int launch_kron(int R, int mode, const KronArgs<T>& a, cudaStream_t s) {
     if (a.b < 1 || a.b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
+    if constexpr (std::is_same<T, float>::value) {
+        if (tiled_ok(a)) {
+            if (R == 3 && mode == KRON_CHEB) return kron_tile_launch<3, KRON_CHEB>(a, s);
+            if (R == 3 && mode == KRON_CHEB_FILT) return kron_tile_launch<3, KRON_CHEB_FILT>(a, s);
+            if (R == 3 && mode == KRON_PLAIN) return kron_tile_launch<3, KRON_PLAIN>(a, s);
+            if (R == 1 && mode == KRON_CHEB) return kron_tile_launch<1, KRON_CHEB>(a, s);
+        }
+    }
     const int shift = tpr_shift_for(a.b);
     const int cpt = (a.b + (1 << shift) - 1) >> shift;
     if (R == 3) {

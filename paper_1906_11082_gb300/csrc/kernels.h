@@ -34,6 +34,14 @@ struct KronArgs {
     T* Z = nullptr;         int64_t ldz = 0;   // FILT accumulator (nullptr: none)
     T a1 = 0, cshift = 0, a2 = 0, gam = 0;
     T sk[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};      // CORI 3x3 (row-major)
+    // optional row tiles (see DevCSR): float operands with b = 32 and
+    // ldx = 32 then gather through shared memory
+    const int* tile_uptr = nullptr;
+    const int* tile_ucol = nullptr;
+    const uint16_t* lcol = nullptr;
+    int tile_rows = 0;
+    int64_t ntiles = 0;
+    int tile_umax = 0;
 };
 
 template <typename T>

@@ -76,6 +76,16 @@ struct DevCSR {
     DevBuf dinv;     // inverse diagonal (scalar square matrices only), double
     DevBuf dinv32;
     std::vector<int32_t> h_rowptr, h_col;   // host copy of the pattern
+    // Row tiles for shared-memory staging of the gathered operand: tile t
+    // holds rows [t*tile_rows, (t+1)*tile_rows); its distinct columns are
+    // tile_ucol[tile_uptr[t] .. tile_uptr[t+1]) and lcol[e] is the position
+    // of col[e] in its tile's list (scalar square matrices only).
+    int tile_rows = 0;
+    int64_t ntiles = 0;
+    int tile_umax = 0;
+    DevBuf tile_uptr;  // int32 [ntiles + 1]
+    DevBuf tile_ucol;  // int32
+    DevBuf lcol;       // uint16 [nnz]
 };
 
 struct Workspace {

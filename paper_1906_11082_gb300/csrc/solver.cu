@@ -32,6 +32,8 @@ struct Mats {
     const T* EG = nullptr;
     const int *et_rp = nullptr, *et_col = nullptr;
     const T* EGt = nullptr;
+    const DevCSR* Mcsr = nullptr;
+    const DevCSR* Pcsr = nullptr;
 };
 
 template <typename T>
@@ -57,6 +59,8 @@ static Mats<T> mats(nm_problem* P) {
     m.AG = vals<T>(P->AG);
     m.Mr = vals<T>(P->Mr);
     m.dM = dinv<T>(P->Mr);
+    m.Mcsr = &P->Mr;
+    m.Pcsr = &P->Pn;
     if (m.Np > 0) {
         m.p_rp = P->Pn.rowptr.as<int>();
         m.p_col = P->Pn.col.as<int>();
@@ -70,6 +74,16 @@ static Mats<T> mats(nm_problem* P) {
         m.EGt = vals<T>(P->EGt);
     }
     return m;
+}
+
+template <typename T>
+static void set_tiles(KronArgs<T>& a, const DevCSR& A) {
+    a.tile_uptr = A.tile_uptr.as<int>();
+    a.tile_ucol = A.tile_ucol.as<int>();
+    a.lcol = A.lcol.as<uint16_t>();
+    a.tile_rows = A.tile_rows;
+    a.ntiles = A.ntiles;
+    a.tile_umax = A.tile_umax;
 }
 
 struct ChebCoef {
@@ -139,6 +153,7 @@ static int schur_pressure(const Mats<T>& m, const T* X, int64_t ldx, int b, int 
         a.col = m.p_col;
         a.val = m.Pn;
         a.dinv = m.dP;
+        set_tiles(a, *m.Pcsr);
         a.b = b;
         a.X = buf[(j - 1) & 1];
         a.ldx = b;
@@ -209,6 +224,7 @@ static int mass_steps(const Mats<T>& m, int b, int k_M, double lo, double hi, co
         a.col = m.u_col;
         a.val = m.Mr;
         a.dinv = m.dM;
+        set_tiles(a, *m.Mcsr);
         a.b = b;
         a.X = buf[(j - 1) & 1];
         a.ldx = b;
@@ -339,6 +355,7 @@ static int cheb32(const DevCSR& A, int R, int b, int k, double lo, double hi, co
         a.col = A.col.as<int>();
         a.val = A.val32.as<float>();
         a.dinv = A.dinv32.as<float>();
+        set_tiles(a, A);
         a.b = b;
         a.X = buf[(j - 1) & 1];
         a.ldx = b;

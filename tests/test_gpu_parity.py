@@ -270,18 +270,67 @@ def test_filter_apply_mixed(nm, planet):
     assert rel_err(to_canonical(P, _host(Z)), ref) <= 1e-8
 
 
-def test_lanczos_slice_planet(planet):
+def _planet_slice_edges(lam, lo_skip=4, count=12):
+    """A slice of seismic modes well above the fluid band, edges in gaps."""
+    hi_sel = lam[lam > 0.5]
+    return 0.5 * (hi_sel[lo_skip - 1] + hi_sel[lo_skip]), 0.5 * (hi_sel[lo_skip + count - 1] + hi_sel[lo_skip + count])
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_lanczos_slice_planet(nm, planet, prec):
+    """Fluid core: the filter must also suppress the fluid's essential
+    spectrum near 0, so the degree follows the slice's distance from it."""
     mesh, model, S, P = planet
     K, M = eig.pencil_dense(S)
     lam = eig.all_eigs(K, M)[0]
-    # a slice of seismic modes well above the fluid band, edges in spectral gaps
-    hi_sel = lam[lam > 0.5]
-    lo_edge = 0.5 * (hi_sel[3] + hi_sel[4])
-    hi_edge = 0.5 * (hi_sel[15] + hi_sel[16])
+    lo_edge, hi_edge = _planet_slice_edges(lam)
     P.set_interval(lo_edge, hi_edge, unit=1)
-    res = P.lanczos_slice(block=8, degree=80, k_M=40, k_P=40, max_blocks=30, seed=2)
+    res = P.lanczos_slice(block=8, degree=400, k_M=40 if prec == "f64" else 20, k_P=40 if prec == "f64" else 20,
+                          max_blocks=30, seed=2, check_every=2,
+                          prec=nm.NM_F64 if prec == "f64" else nm.NM_MIXED)
     ref = lam[(lam >= lo_edge) & (lam <= hi_edge)]
     _check_slice(res, ref, lam[-1])
+
+
+def test_ritz_rotating_matches_oracle(nm, ctx):
+    """Rotating reduction (eq. sublinear0) on the Ritz vectors of a slice:
+    the eigenvalues depend only on the slice's eigenspace, so the GPU's
+    (its own Lanczos vectors) and the oracle's (dense eigenvectors) agree."""
+    from synth.model import homogeneous_ball
+    mesh, model = homogeneous_ball(h=0.45, seed=1)
+    model.Omega = np.array([0.0, 0.0, 0.05])
+    S = fem.assemble(mesh, model)
+    P = nm.Problem(ctx, mesh, model)
+    P.set_interval(2.0, 3.0)
+    res = P.lanczos_slice(block=8, degree=100, k_M=40, k_P=40, max_blocks=16, seed=3)
+    K, M = eig.pencil_dense(S)
+    lam, Xd = eig.all_eigs(K, M)
+    sel = (lam >= 4.0) & (lam <= 9.0)
+    assert len(res.lam) == sel.sum() == 10
+    X = res.vectors()
+    P.set_interval(2.0, 2.9)
+    rot = P.ritz(X, mode=nm.NM_RITZ_ROTATING, lam_e=res.lam)
+    Q = Xd[:, sel].T @ (S.R @ Xd[:, sel])
+    wr, _ = eig.rotating_reduced(lam[sel], Q)
+    ref = np.sort(wr[(wr >= 2.0) & (wr <= 2.9)])
+    assert len(rot.lam) == len(ref) and len(ref) > 0
+    assert np.allclose(np.sort(rot.lam), ref, rtol=1e-9)
+    # the complex eigenvectors are returned; the full quadratic residual is reported
+    U = rot.vectors()
+    assert U.dtype == torch.complex128 and U.shape == (S.n, len(ref))
+    assert np.isfinite(rot.resid).all() and rot.resid.max() < 1e-2
+
+
+def test_ritz_rotating_zero_omega(nm, ctx):
+    """Omega = 0: omega_e = Lambda_e^{1/2} exactly (Sec. 7)."""
+    from synth.model import homogeneous_ball
+    mesh, model = homogeneous_ball(h=0.45, seed=1)
+    P = nm.Problem(ctx, mesh, model)
+    P.set_interval(2.0, 3.0)
+    res = P.lanczos_slice(block=8, degree=100, k_M=40, k_P=40, max_blocks=16, seed=3)
+    rot = P.ritz(res.vectors(), mode=nm.NM_RITZ_ROTATING, lam_e=res.lam)
+    assert np.allclose(np.sort(rot.lam), np.sort(np.sqrt(res.lam)), rtol=1e-12)
+    assert rot.resid.max() <= 1e-6
 
 
 def test_empty_slice_reports_not_converged(nm, ball):

@@ -405,3 +405,63 @@ def test_lanczos_slice_matches_dense(ball):
     # cross-check the residual with the dense pencil
     r2 = eig.residuals(K, M, got, X, floor=filtlan.residual_floor(lam_lo, lam_hi))
     assert r2.max() <= 1e-6
+
+
+# ------------------------------------------------------------ rotation
+def _ball_T2(h, omega):
+    mesh, model = homogeneous_ball(h=h, seed=1)
+    model.Omega = np.array([0.0, 0.0, omega])
+    S = fem.assemble(mesh, model)
+    w, X = eig.eigs_near(S, 2.55 ** 2, 16)
+    o = np.argsort(w)
+    w, X = w[o], X[:, o]
+    sel = w > 1.0
+    return S, w[sel], X[:, sel]
+
+
+def test_coriolis_matrix_skew():
+    mesh, model = layered_planet(h=0.25, seed=7, omega=0.3)
+    S = fem.assemble(mesh, model)
+    assert abs(S.R + S.R.T).max() <= 1e-15 * abs(S.R).max()
+    x = np.random.default_rng(0).standard_normal(S.n)
+    assert abs(x @ (S.R @ x)) <= 1e-12 * np.linalg.norm(x) ** 2 * abs(S.R).max()
+
+
+def test_toroidal_coriolis_splitting():
+    """First-order Coriolis splitting of a toroidal multiplet of a
+    homogeneous ball: omega_m = omega_0 + m Omega / (l (l+1)), so the
+    Hermitian matrix i X^T R X on the 0T2 eigenspace has eigenvalues
+    m Omega / 6, m = -2..2 (basis independent)."""
+    omega = 0.05
+    errs = []
+    for h in (0.45, 0.3):
+        S, w, X = _ball_T2(h, omega)
+        T2 = X[:, :5]
+        ev = np.sort(np.linalg.eigvalsh(1j * (T2.T @ (S.R @ T2)))) * 6.0 / omega
+        errs.append(np.abs(ev - np.arange(-2, 3)).max())
+    assert errs[1] < errs[0] < 0.05 and errs[1] < 0.01
+
+
+def test_rotating_reduction_identities():
+    S, w, X = _ball_T2(0.45, 0.05)
+    Xe, lam = X[:, :10], w[:10]
+    # Omega = 0: omega_e = sqrt(Lambda_e) exactly (Sec. 7)
+    wr0, _ = eig.rotating_reduced(lam, np.zeros((10, 10)))
+    assert np.allclose(np.sort(wr0[wr0 > 0]), np.sqrt(lam), rtol=1e-13)
+    # rotating: real spectrum in +- pairs
+    Q = Xe.T @ (S.R @ Xe)
+    wr, Y = eig.rotating_reduced(lam, Q)
+    assert np.allclose(np.sort(wr), -np.sort(wr)[::-1], atol=1e-12)
+    # orthogonality in the rotating inner product (eq. orthonormalcond):
+    # b_H(u_i, u_j) - 2i (w_i + w_j)^{-1} c_r(u_i, u_j) = 0 for i != j
+    pos = np.nonzero(wr > 0)[0]
+    U = Xe @ Y[:10, pos]
+    Mu = S.M @ U
+    Ru = S.R @ U
+    B = U.conj().T @ Mu
+    Cr = U.conj().T @ Ru
+    wi = wr[pos]
+    G = B - 2j * Cr / (wi[:, None] + wi[None, :])
+    off = G - np.diag(np.diag(G))
+    assert np.abs(off).max() <= 1e-10 * np.abs(np.diag(G)).max()
+    assert (np.diag(G).real > 0).all()
