@@ -136,6 +136,7 @@ typedef struct {
     uint64_t seed;        /* start block seed (counter-based Philox-4x32-10) */
     const double* start;  /* optional device start block (n x block, ld=block); NULL: drawn from seed */
     int32_t bounds_steps; /* Lanczos steps for the spectrum bounds (0: 40)   */
+    int32_t log_every;    /* > 0: one progress line on stderr every that many blocks */
 } nm_slice_opts;
 
 /* ---- context ---------------------------------------------------------- */
@@ -174,6 +175,22 @@ int nm_problem_unodes(const nm_problem* prob, int64_t* canon, int64_t* p2, int64
  * col[nnz], vals[nnz * block entries]. */
 int nm_problem_export(const nm_problem* prob, int which, int64_t* nrows, int64_t* nnz,
                       int64_t* rowptr, int32_t* col, double* vals);
+
+/* Tuning knobs of a problem (the autotuner's hooks). key "sched": 1
+ * (default) runs the semi-iteration SpMMs of blocks 17..64 wide as
+ * persistent SM-local kernels (each SM walks its own contiguous range of
+ * Morton-ordered rows, so neighbour gathers hit in L1); 0 uses one thread
+ * group per row over a plain grid. key "tile_rows": height of the row
+ * tiles whose gathered operand the float kernels stage in shared memory
+ * (0, the default, disables staging; 4..64, power of two); the tiles are
+ * rebuilt on the host. key "tile_kernel": 1 or 2, the staged kernel
+ * variant (256-thread rounds / 512-thread unrolled rounds). key
+ * "double_float": 1 (default) runs the NM_MIXED form's double-precision
+ * SpMMs (the K_eff block SpMM and the refinement residuals) as
+ * double-float arithmetic on the float units (values split exactly into
+ * two floats, error-free products and sums, ~2^-48 relative); 0 runs them
+ * in double. NM_EINVAL for an unknown key or value. */
+int nm_set_option(nm_problem* prob, const char* key, int64_t value);
 
 /* Reference field g' at the internal u-nodes (host out, 3*Nu doubles). */
 int nm_problem_gravity(const nm_problem* prob, double* g);

@@ -36,6 +36,7 @@ int lanczos_slice(nm_problem* P, const nm_slice_opts* o, nm_result** out);
 int ritz(nm_problem* P, nm_ritz_mode mode, const double* V, int64_t ldv, int m, const double* lam_e,
          nm_result** out);
 int profile_read(nm_problem* P, int kind, int64_t* launches, double* ms);
+int set_tile_rows(nm_problem* P, int64_t rows);
 int profile_set(nm_problem* P, int enable, int reset);
 
 uint64_t launches_so_far();
@@ -199,6 +200,31 @@ int nm_problem_export(const nm_problem* P, int which, int64_t* nrows, int64_t* n
         if (e != cudaSuccess) return fail(NM_ECUDA, cudaGetErrorString(e));
     }
     return NM_OK;
+}
+
+int nm_set_option(nm_problem* P, const char* key, int64_t value) {
+    if (!P || !key) return fail(NM_EINVAL, "null argument");
+    CtxScope sc(P->ctx);
+    if (std::string(key) == "tile_rows") {
+        cudaStreamSynchronize(P->ctx->stream);
+        return set_tile_rows(P, value);
+    }
+    if (std::string(key) == "sched") {
+        if (value != 0 && value != 1) return fail(NM_EINVAL, "sched must be 0 or 1");
+        P->use_sched = (int)value;
+        return NM_OK;
+    }
+    if (std::string(key) == "double_float") {
+        if (value != 0 && value != 1) return fail(NM_EINVAL, "double_float must be 0 or 1");
+        P->use_df = (int)value;
+        return NM_OK;
+    }
+    if (std::string(key) == "tile_kernel") {
+        if (value != 1 && value != 2) return fail(NM_EINVAL, "tile_kernel must be 1 or 2");
+        P->Mr.tile_kernel = P->Pn.tile_kernel = (int)value;
+        return NM_OK;
+    }
+    return fail(NM_EINVAL, std::string("unknown option: ") + key);
 }
 
 int nm_problem_gravity(const nm_problem* P, double* g) {

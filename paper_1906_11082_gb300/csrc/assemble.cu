@@ -557,13 +557,23 @@ static int build_tiles(DevCSR& A, int rows) {
     return NM_OK;
 }
 
-// Largest tile height (power of two, <= 64) whose staged float operand of
-// b = 32 columns and R sub-rows fits `budget` bytes of shared memory.
-static int pick_tiles(DevCSR& A, int R, size_t budget) {
-    for (int rows = 64; rows >= 4; rows /= 2) {
-        NM_TRY(build_tiles(A, rows));
-        if ((size_t)A.tile_umax * R * 32 * sizeof(float) <= budget) return NM_OK;
+int set_tile_rows(nm_problem* P, int64_t rows) {
+    if (rows == 0) {
+        for (DevCSR* A : {&P->Mr, &P->Pn}) {
+            A->tile_uptr.release();
+            A->tile_ucol.release();
+            A->lcol.release();
+            A->tile_rows = 0;
+            A->ntiles = 0;
+            A->tile_umax = 0;
+        }
+        return NM_OK;
     }
+    if (rows < 4 || rows > 64 || (rows & (rows - 1))) return fail(NM_EINVAL, "tile_rows must be 0 or 4..64, a power of two");
+    NM_TRY(build_tiles(P->Mr, (int)rows));
+    if (P->info.Np > 0) NM_TRY(build_tiles(P->Pn, (int)rows));
+    if ((size_t)P->Mr.tile_umax * 3 * 32 * sizeof(float) > 200 * 1024)
+        return fail(NM_EINVAL, "tile_rows too large: staged operand exceeds shared memory");
     return NM_OK;
 }
 
@@ -933,8 +943,14 @@ int assemble(nm_ctx* ctx, const nm_mesh* mesh, const nm_model* mdl, nm_problem* 
     NM_CUDA(cudaStreamSynchronize(s));
     NM_TRY(make_dinv(P->Mr));
     if (Np > 0) NM_TRY(make_dinv(P->Pn));
-    NM_TRY(pick_tiles(P->Mr, 3, 100 * 1024));
-    if (Np > 0) NM_TRY(pick_tiles(P->Pn, 1, 100 * 1024));
+    // region counters of the SM-local schedule (one per SM)
+    {
+        int dev = 0, sms = 0;
+        NM_CUDA(cudaGetDevice(&dev));
+        NM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        P->nreg = sms > 0 ? sms : 1;
+        NM_TRY(P->sched.alloc((size_t)P->nreg * sizeof(int)));
+    }
     NM_CUDA(cudaStreamSynchronize(s));
 
     auto& I = P->info;
@@ -950,6 +966,28 @@ int assemble(nm_ctx* ctx, const nm_mesh* mesh, const nm_model* mdl, nm_problem* 
     I.n_fs = nfs;
     P->flags = mdl->flags;
     for (int d = 0; d < 3; ++d) P->Omega[d] = mdl->Omega[d];
+    return NM_OK;
+}
+
+__global__ void lo_part_kernel(int64_t n, const double* v, const float* hi, float* lo) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        lo[t] = __double2float_rn(v[t] - (double)hi[t]);
+}
+
+int ensure_f32(nm_problem* P, cudaStream_t s);
+
+// Low float parts of the matrix values for the double-float kernels.
+int ensure_df(nm_problem* P, cudaStream_t s) {
+    NM_TRY(ensure_f32(P, s));
+    for (DevCSR* A : {&P->AG, &P->Mr, &P->Pn}) {
+        if (A->nnz == 0 || A->vlo32.p) continue;
+        const int64_t cnt = A->nnz * A->rb * A->cb;
+        NM_TRY(A->vlo32.alloc(cnt * sizeof(float)));
+        lo_part_kernel<<<(unsigned)std::min<int64_t>((cnt + 255) / 256, 4864), 256, 0, s>>>(
+            cnt, A->val.as<double>(), A->val32.as<float>(), A->vlo32.as<float>());
+        count_launch();
+        NM_CUDA(cudaGetLastError());
+    }
     return NM_OK;
 }
 

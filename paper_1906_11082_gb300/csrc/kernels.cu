@@ -168,6 +168,73 @@ __global__ void __launch_bounds__(kThreads) kron_tile_kernel(const KronArgs<floa
     }
 }
 
+// Second tiled variant: 512 threads (16 warps) per CTA, the (value, local
+// column) pairs of a round consumed four at a time with two accumulator
+// sets, so each warp keeps eight shared-memory loads in flight.
+template <int R, int MODE>
+__global__ void __launch_bounds__(512) kron_tile2_kernel(const KronArgs<float> a) {
+    extern __shared__ float4 kron_smem4[];
+    float* xs = reinterpret_cast<float*>(kron_smem4);
+    constexpr int RB = R * 32;
+    constexpr int PER = RB / 4;
+    constexpr int NT = 512;
+    const int64_t t = blockIdx.x;
+    const int u0 = __ldg(a.tile_uptr + t);
+    const int U = __ldg(a.tile_uptr + t + 1) - u0;
+    for (int i = threadIdx.x; i < U * PER; i += NT) {
+        const int u = i / PER, q = i - u * PER;
+        const int64_t node = __ldg(a.tile_ucol + u0 + u);
+        const int k = (4 * q) >> 5, cc = (4 * q) & 31;
+        const float* src = a.X + ((int64_t)R * node + k) * 32 + cc;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(xs + u * RB + 4 * q);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int rr = warp; rr < a.tile_rows; rr += NT / 32) {
+        const int64_t row = t * a.tile_rows + rr;
+        if (row >= a.nrows) break;
+        float acc[R], acc2[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[k] = acc2[k] = 0.f;
+        const int e0 = __ldg(a.rowptr + row), e1 = __ldg(a.rowptr + row + 1);
+        for (int base = e0; base < e1; base += 32) {
+            const int e = base + lane;
+            const float vr = e < e1 ? __ldg(a.val + e) : 0.f;
+            const int lr = e < e1 ? (int)__ldg(a.lcol + e) : 0;
+            const int cnt = min(32, e1 - base);
+            int j = 0;
+            for (; j + 4 <= cnt; j += 4) {
+                const float v0 = __shfl_sync(0xffffffffu, vr, j), v1 = __shfl_sync(0xffffffffu, vr, j + 1);
+                const float v2 = __shfl_sync(0xffffffffu, vr, j + 2), v3 = __shfl_sync(0xffffffffu, vr, j + 3);
+                const float* x0 = xs + __shfl_sync(0xffffffffu, lr, j) * RB + lane;
+                const float* x1 = xs + __shfl_sync(0xffffffffu, lr, j + 1) * RB + lane;
+                const float* x2 = xs + __shfl_sync(0xffffffffu, lr, j + 2) * RB + lane;
+                const float* x3 = xs + __shfl_sync(0xffffffffu, lr, j + 3) * RB + lane;
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const float a0 = x0[32 * k], a1 = x1[32 * k], a2 = x2[32 * k], a3 = x3[32 * k];
+                    acc[k] = fmaf(v0, a0, acc[k]);
+                    acc2[k] = fmaf(v1, a1, acc2[k]);
+                    acc[k] = fmaf(v2, a2, acc[k]);
+                    acc2[k] = fmaf(v3, a3, acc2[k]);
+                }
+            }
+            for (; j < cnt; ++j) {
+                const float v = __shfl_sync(0xffffffffu, vr, j);
+                const float* x = xs + __shfl_sync(0xffffffffu, lr, j) * RB + lane;
+#pragma unroll
+                for (int k = 0; k < R; ++k) acc[k] = fmaf(v, x[32 * k], acc[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[k] += acc2[k];
+        kron_epilogue<float, R, MODE>(a, row, lane, acc);
+    }
+}
+
 template <int R, int MODE>
 static int kron_tile_launch(const KronArgs<float>& a, cudaStream_t s) {
     const size_t smem = (size_t)a.tile_umax * R * 32 * sizeof(float);
@@ -175,9 +242,101 @@ static int kron_tile_launch(const KronArgs<float>& a, cudaStream_t s) {
     if (!attr_set) {
         NM_CUDA(cudaFuncSetAttribute(kron_tile_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      200 * 1024));
+        NM_CUDA(cudaFuncSetAttribute(kron_tile2_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     200 * 1024));
         attr_set = true;
     }
-    kron_tile_kernel<R, MODE><<<(unsigned)a.ntiles, kThreads, smem, s>>>(a);
+    if (a.tile_kernel == 2)
+        kron_tile2_kernel<R, MODE><<<(unsigned)a.ntiles, 512, smem, s>>>(a);
+    else
+        kron_tile_kernel<R, MODE><<<(unsigned)a.ntiles, kThreads, smem, s>>>(a);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+// SM-local persistent variant for full-warp groups (b = 32 or 64): the rows
+// are split into nreg contiguous regions (one per SM); each CTA reads its SM
+// id and takes groups of 8 consecutive rows of that SM's region from a
+// region counter, then moves on to the following regions (so every row is
+// done even if some SM runs no CTA). All CTAs resident on an SM therefore
+// walk adjacent Morton-ordered rows and share their neighbours in L1. The
+// (value, column) pairs of a row are read 32 at a time by the warp and
+// broadcast with shuffles.
+template <typename T, int R, int CPT, int MODE>
+__global__ void __launch_bounds__(kThreads) kron_sm_kernel(const KronArgs<T> a) {
+    __shared__ int sh_group;
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    constexpr int GROUP = kThreads / 32;
+    const int64_t N = a.nrows;
+    for (int k = 0; k < a.nreg; ++k) {
+        const int reg = (int)((smid + k) % (unsigned)a.nreg);
+        const int64_t r0 = N * reg / a.nreg, r1 = N * (reg + 1) / a.nreg;
+        const int64_t ngroups = (r1 - r0 + GROUP - 1) / GROUP;
+        for (;;) {
+            __syncthreads();
+            if (threadIdx.x == 0) sh_group = atomicAdd(a.sched + reg, 1);
+            __syncthreads();
+            const int64_t g = sh_group;
+            if (g >= ngroups) break;
+            const int64_t row = r0 + g * GROUP + warp;
+            if (row >= r1) continue;
+            T acc[CPT][R];
+#pragma unroll
+            for (int q = 0; q < CPT; ++q)
+#pragma unroll
+                for (int kk = 0; kk < R; ++kk) acc[q][kk] = T(0);
+            const int e0 = __ldg(a.rowptr + row), e1 = __ldg(a.rowptr + row + 1);
+            for (int base = e0; base < e1; base += 32) {
+                const int e = base + lane;
+                const T vr = e < e1 ? __ldg(a.val + e) : T(0);
+                const int cr = e < e1 ? __ldg(a.col + e) : 0;
+                const int cnt = min(32, e1 - base);
+                for (int jj = 0; jj < cnt; ++jj) {
+                    const T v = __shfl_sync(0xffffffffu, vr, jj);
+                    const int64_t j = __shfl_sync(0xffffffffu, cr, jj);
+                    const T* xj = a.X + (int64_t)R * j * a.ldx;
+#pragma unroll
+                    for (int q = 0; q < CPT; ++q) {
+                        const int c = lane + 32 * q;
+                        if (c < a.b) {
+#pragma unroll
+                            for (int kk = 0; kk < R; ++kk) acc[q][kk] += v * __ldg(xj + kk * a.ldx + c);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                const int c = lane + 32 * q;
+                if (c < a.b) kron_epilogue<T, R, MODE>(a, row, c, acc[q]);
+            }
+        }
+    }
+}
+
+template <typename T, int R, int MODE>
+static int kron_sm_launch(const KronArgs<T>& a, cudaStream_t s) {
+    static int grid[2] = {0, 0};
+    const int cpt = a.b > 32 ? 2 : 1;
+    if (grid[cpt - 1] == 0) {
+        int dev = 0, sms = 0, per = 0;
+        NM_CUDA(cudaGetDevice(&dev));
+        NM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (cpt == 1)
+            NM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kron_sm_kernel<T, R, 1, MODE>, kThreads, 0));
+        else
+            NM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kron_sm_kernel<T, R, 2, MODE>, kThreads, 0));
+        grid[cpt - 1] = sms * (per > 0 ? per : 1);
+    }
+    NM_CUDA(cudaMemsetAsync(a.sched, 0, a.nreg * sizeof(int), s));
+    if (cpt == 1)
+        kron_sm_kernel<T, R, 1, MODE><<<grid[0], kThreads, 0, s>>>(a);
+    else
+        kron_sm_kernel<T, R, 2, MODE><<<grid[1], kThreads, 0, s>>>(a);
     count_launch();
     NM_CUDA(cudaGetLastError());
     return NM_OK;
@@ -185,7 +344,7 @@ static int kron_tile_launch(const KronArgs<float>& a, cudaStream_t s) {
 
 template <typename T>
 static bool tiled_ok(const KronArgs<T>& a) {
-    if (!std::is_same<T, float>::value || !a.tile_uptr || a.b != 32 || a.ldx != 32) return false;
+    if (!std::is_same<T, float>::value || !a.tile_uptr || a.ntiles == 0 || a.b != 32 || a.ldx != 32) return false;
     if (((uintptr_t)a.X & 15) != 0) return false;
     return (size_t)a.tile_umax * 3 * 32 * sizeof(float) <= 200 * 1024;
 }
@@ -193,6 +352,18 @@ static bool tiled_ok(const KronArgs<T>& a) {
 template <typename T>
 int launch_kron(int R, int mode, const KronArgs<T>& a, cudaStream_t s) {
     if (a.b < 1 || a.b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
+    if (a.sched && a.nreg > 0 && a.b >= 17 && a.b <= 64) {
+        if (R == 3) {
+            switch (mode) {
+                case KRON_PLAIN: return kron_sm_launch<T, 3, KRON_PLAIN>(a, s);
+                case KRON_CHEB: return kron_sm_launch<T, 3, KRON_CHEB>(a, s);
+                case KRON_CHEB_FILT: return kron_sm_launch<T, 3, KRON_CHEB_FILT>(a, s);
+                case KRON_CORI: return kron_sm_launch<T, 3, KRON_CORI>(a, s);
+            }
+        } else if (R == 1 && mode == KRON_CHEB) {
+            return kron_sm_launch<T, 1, KRON_CHEB>(a, s);
+        }
+    }
     if constexpr (std::is_same<T, float>::value) {
         if (tiled_ok(a)) {
             if (R == 3 && mode == KRON_CHEB) return kron_tile_launch<3, KRON_CHEB>(a, s);
@@ -572,6 +743,179 @@ __global__ void combine_kernel(const CombineArgs a) {
 int launch_combine(const CombineArgs& a, cudaStream_t s) {
     if (a.rows * a.b == 0) return NM_OK;
     combine_kernel<<<grid_for(a.rows * a.b), kThreads, 0, s>>>(a);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+// ----------------------------------------------------------------- double-float
+// sh + sl += (ah + al)(xh + xl) to ~2^-48: TwoProduct of the leading terms by
+// FMA, the cross terms by FMA, TwoSum into the leading accumulator and a
+// FastTwoSum renormalisation. The _rn intrinsics keep the compiler from
+// contracting or reassociating the error-free transformations.
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al, float xh, float xl) {
+    const float p = __fmul_rn(ah, xh);
+    const float e = __fmaf_rn(ah, xh, -p);
+    const float t = __fmaf_rn(ah, xl, __fmaf_rn(al, xh, e));
+    const float s = __fadd_rn(sh, p);
+    const float bp = __fadd_rn(s, -sh);
+    const float err = __fadd_rn(__fadd_rn(sh, -__fadd_rn(s, -bp)), __fadd_rn(p, -bp));
+    const float lo = __fadd_rn(__fadd_rn(sl, err), t);
+    sh = __fadd_rn(s, lo);
+    sl = __fadd_rn(lo, -__fadd_rn(sh, s));
+}
+
+__global__ void split_kernel(int64_t rows, int b, const double* X, int64_t ldx, float* Xh, float* Xl) {
+    const int64_t total = rows * b;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / b;
+        const int c = (int)(t - i * b);
+        const double x = X[i * ldx + c];
+        const float h = __double2float_rn(x);
+        Xh[t] = h;
+        Xl[t] = __double2float_rn(x - (double)h);
+    }
+}
+
+template <int CPT>
+__global__ void __launch_bounds__(kThreads) bsr33_df_kernel(const Bsr33DfArgs a, int tpr_shift) {
+    const int tpr = 1 << tpr_shift;
+    const int lane = threadIdx.x & (tpr - 1);
+    const int64_t row = (int64_t)blockIdx.x * (kThreads >> tpr_shift) + (threadIdx.x >> tpr_shift);
+    if (row >= a.nrows) return;
+    float sh[CPT][3], sl[CPT][3];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) sh[q][m] = sl[q][m] = 0.f;
+    const int e0 = __ldg(a.rowptr + row), e1 = __ldg(a.rowptr + row + 1);
+    for (int e = e0; e < e1; ++e) {
+        const int64_t j = __ldg(a.col + e);
+        float kh[9], kl[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            kh[t] = __ldg(a.vh + 9 * (int64_t)e + t);
+            kl[t] = __ldg(a.vl + 9 * (int64_t)e + t);
+        }
+        const int64_t base = 3 * j * a.b;
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int c = lane + q * tpr;
+            if (c < a.b) {
+                float xh[3], xl[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    xh[k] = __ldg(a.Xh + base + k * a.b + c);
+                    xl[k] = __ldg(a.Xl + base + k * a.b + c);
+                }
+#pragma unroll
+                for (int m = 0; m < 3; ++m)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) df_fma(sh[q][m], sl[q][m], kh[3 * m + k], kl[3 * m + k], xh[k], xl[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int c = lane + q * tpr;
+        if (c >= a.b) continue;
+        double acc[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) acc[m] = (double)sh[q][m] + (double)sl[q][m];
+        if (a.e_rowptr) {
+            const int f0 = __ldg(a.e_rowptr + row), f1 = __ldg(a.e_rowptr + row + 1);
+            for (int e = f0; e < f1; ++e) {
+                const int64_t p = __ldg(a.e_col + e);
+                const double sv = __ldg(a.S + p * a.lds + c);
+#pragma unroll
+                for (int m = 0; m < 3; ++m) acc[m] += __ldg(a.e_val + 3 * (int64_t)e + m) * sv;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 3; ++m) a.W[(3 * row + m) * a.ldw + c] = acc[m];
+    }
+}
+
+template <int R, int CPT>
+__global__ void __launch_bounds__(kThreads) resid_df_kernel(int64_t nodes, const int* __restrict__ rowptr,
+                                                            const int* __restrict__ col, const float* __restrict__ vh,
+                                                            const float* __restrict__ vl, const double* __restrict__ W,
+                                                            int64_t ldw, const float* __restrict__ x, float* r, int b,
+                                                            int tpr_shift) {
+    const int tpr = 1 << tpr_shift;
+    const int lane = threadIdx.x & (tpr - 1);
+    const int64_t row = (int64_t)blockIdx.x * (kThreads >> tpr_shift) + (threadIdx.x >> tpr_shift);
+    if (row >= nodes) return;
+    float sh[CPT][R], sl[CPT][R];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q)
+#pragma unroll
+        for (int k = 0; k < R; ++k) sh[q][k] = sl[q][k] = 0.f;
+    const int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
+    for (int e = e0; e < e1; ++e) {
+        const int64_t j = __ldg(col + e);
+        const float mh = __ldg(vh + e), ml = __ldg(vl + e);
+        const float* xj = x + (int64_t)R * j * b;
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int c = lane + q * tpr;
+            if (c < b) {
+#pragma unroll
+                for (int k = 0; k < R; ++k) df_fma(sh[q][k], sl[q][k], mh, ml, __ldg(xj + k * b + c), 0.f);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int c = lane + q * tpr;
+        if (c >= b) continue;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int64_t rr = R * row + k;
+            r[rr * b + c] = (float)((W[rr * ldw + c] - (double)sh[q][k]) - (double)sl[q][k]);
+        }
+    }
+}
+
+int launch_split(int64_t rows, int b, const double* X, int64_t ldx, float* Xh, float* Xl, cudaStream_t s) {
+    if (rows * b == 0) return NM_OK;
+    split_kernel<<<grid_for(rows * b), kThreads, 0, s>>>(rows, b, X, ldx, Xh, Xl);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+int launch_bsr33_df(const Bsr33DfArgs& a, cudaStream_t s) {
+    if (a.b < 1 || a.b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
+    const int shift = tpr_shift_for(a.b);
+    const int cpt = (a.b + (1 << shift) - 1) >> shift;
+    const int64_t grid = (a.nrows + (kThreads >> shift) - 1) / (kThreads >> shift);
+    if (grid == 0) return NM_OK;
+    if (cpt == 1)
+        bsr33_df_kernel<1><<<(unsigned)grid, kThreads, 0, s>>>(a, shift);
+    else
+        bsr33_df_kernel<2><<<(unsigned)grid, kThreads, 0, s>>>(a, shift);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+int launch_resid_df(int R, int64_t nodes, const int* rowptr, const int* col, const float* vh, const float* vl,
+                    const double* W, int64_t ldw, const float* x32, float* r32, int b, cudaStream_t s) {
+    if (b < 1 || b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
+    const int shift = tpr_shift_for(b);
+    const int cpt = (b + (1 << shift) - 1) >> shift;
+    const int64_t grid = (nodes + (kThreads >> shift) - 1) / (kThreads >> shift);
+    if (grid == 0) return NM_OK;
+    if (R == 3 && cpt == 1)
+        resid_df_kernel<3, 1><<<(unsigned)grid, kThreads, 0, s>>>(nodes, rowptr, col, vh, vl, W, ldw, x32, r32, b, shift);
+    else if (R == 3)
+        resid_df_kernel<3, 2><<<(unsigned)grid, kThreads, 0, s>>>(nodes, rowptr, col, vh, vl, W, ldw, x32, r32, b, shift);
+    else if (cpt == 1)
+        resid_df_kernel<1, 1><<<(unsigned)grid, kThreads, 0, s>>>(nodes, rowptr, col, vh, vl, W, ldw, x32, r32, b, shift);
+    else
+        resid_df_kernel<1, 2><<<(unsigned)grid, kThreads, 0, s>>>(nodes, rowptr, col, vh, vl, W, ldw, x32, r32, b, shift);
     count_launch();
     NM_CUDA(cudaGetLastError());
     return NM_OK;

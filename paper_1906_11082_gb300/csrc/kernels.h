@@ -42,6 +42,11 @@ struct KronArgs {
     int tile_rows = 0;
     int64_t ntiles = 0;
     int tile_umax = 0;
+    int tile_kernel = 2;   // 1: 256-thread rounds, 2: 512-thread unrolled rounds
+    // SM-local persistent schedule (b = 32 or 64): nreg region counters,
+    // zeroed by the launcher on the stream before the launch
+    int* sched = nullptr;
+    int nreg = 0;
 };
 
 template <typename T>
@@ -117,6 +122,34 @@ struct CombineArgs {
     double a1 = 0, cshift = 0, a2 = 0, gam = 0;
 };
 int launch_combine(const CombineArgs& a, cudaStream_t s);
+
+// Double-float forms (value = hi + lo, two floats, ~2^-48 relative): the
+// K_eff SpMM and the refinement residual on the float units.
+// Split a double block into exact float pairs (hi = fl(x), lo = fl(x - hi)).
+int launch_split(int64_t rows, int b, const double* X, int64_t ldx, float* Xh, float* Xl, cudaStream_t s);
+// W = A X + E S with A's 3x3 blocks as (hi, lo) floats and X as (hi, lo)
+// float blocks (ld b), double-float sums; the optional E S part in double.
+struct Bsr33DfArgs {
+    int nrows = 0;
+    const int* rowptr = nullptr;
+    const int* col = nullptr;
+    const float* vh = nullptr;
+    const float* vl = nullptr;
+    const float* Xh = nullptr;
+    const float* Xl = nullptr;
+    int b = 0;
+    const int* e_rowptr = nullptr;
+    const int* e_col = nullptr;
+    const double* e_val = nullptr;
+    const double* S = nullptr;
+    int64_t lds = 0;
+    double* W = nullptr;
+    int64_t ldw = 0;
+};
+int launch_bsr33_df(const Bsr33DfArgs& a, cudaStream_t s);
+// r32 = float(W - (A (x) I_R) x32) with A as (hi, lo) floats, double-float sums.
+int launch_resid_df(int R, int64_t nodes, const int* rowptr, const int* col, const float* vh, const float* vl,
+                    const double* W, int64_t ldw, const float* x32, float* r32, int b, cudaStream_t s);
 
 // Y[i, c] = alpha * X[i, c] (rows x b, row-major with leading dims).
 template <typename T>

@@ -72,7 +72,8 @@ struct DevCSR {
     DevBuf rowptr;   // int32 [nrows + 1]  (nnz < 2^31 checked at build)
     DevBuf col;      // int32 [nnz]
     DevBuf val;      // double [nnz * rb * cb]
-    DevBuf val32;    // float  [nnz * rb * cb] (on demand)
+    DevBuf val32;    // float  [nnz * rb * cb] (on demand): fl(val), the high part
+    DevBuf vlo32;    // float  [nnz * rb * cb] (on demand): fl(val - fl(val)), the low part
     DevBuf dinv;     // inverse diagonal (scalar square matrices only), double
     DevBuf dinv32;
     std::vector<int32_t> h_rowptr, h_col;   // host copy of the pattern
@@ -83,6 +84,7 @@ struct DevCSR {
     int tile_rows = 0;
     int64_t ntiles = 0;
     int tile_umax = 0;
+    int tile_kernel = 2;
     DevBuf tile_uptr;  // int32 [ntiles + 1]
     DevBuf tile_ucol;  // int32
     DevBuf lcol;       // uint16 [nnz]
@@ -130,6 +132,12 @@ struct nm_problem {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_regions;  // kind, (start, stop)
     std::vector<int64_t> ev_launches;   // launches inside each region
     size_t ev_next = 0;
+    // mixed form: K_eff SpMM and refinement residuals in double-float
+    int use_df = 1;
+    // SM-local persistent schedule of the semi-iteration kernels
+    int use_sched = 1;
+    nm::DevBuf sched;   // int [nreg] region counters
+    int nreg = 0;
     // scratch for the filter recurrence
     nm::Workspace ws;
     nm::DevBuf pscratch;     // pressure-sized scratch for the Schur term

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <complex>
 #include <memory>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -17,6 +18,7 @@
 namespace nm {
 
 int ensure_f32(nm_problem* P, cudaStream_t s);
+int ensure_df(nm_problem* P, cudaStream_t s);
 
 static const double kMassLo = 0.25;
 static const double kMassHi = (19.0 + 15.779733838059499) / 8.0;   // (19 + sqrt(249)) / 8
@@ -34,6 +36,7 @@ struct Mats {
     const T* EGt = nullptr;
     const DevCSR* Mcsr = nullptr;
     const DevCSR* Pcsr = nullptr;
+    nm_problem* P = nullptr;
 };
 
 template <typename T>
@@ -61,6 +64,7 @@ static Mats<T> mats(nm_problem* P) {
     m.dM = dinv<T>(P->Mr);
     m.Mcsr = &P->Mr;
     m.Pcsr = &P->Pn;
+    m.P = P;
     if (m.Np > 0) {
         m.p_rp = P->Pn.rowptr.as<int>();
         m.p_col = P->Pn.col.as<int>();
@@ -77,6 +81,14 @@ static Mats<T> mats(nm_problem* P) {
 }
 
 template <typename T>
+static void set_sched(KronArgs<T>& a, nm_problem* P) {
+    if (P->use_sched && P->sched.p) {
+        a.sched = P->sched.as<int>();
+        a.nreg = P->nreg;
+    }
+}
+
+template <typename T>
 static void set_tiles(KronArgs<T>& a, const DevCSR& A) {
     a.tile_uptr = A.tile_uptr.as<int>();
     a.tile_ucol = A.tile_ucol.as<int>();
@@ -84,6 +96,7 @@ static void set_tiles(KronArgs<T>& a, const DevCSR& A) {
     a.tile_rows = A.tile_rows;
     a.ntiles = A.ntiles;
     a.tile_umax = A.tile_umax;
+    a.tile_kernel = A.tile_kernel;
 }
 
 struct ChebCoef {
@@ -154,6 +167,7 @@ static int schur_pressure(const Mats<T>& m, const T* X, int64_t ldx, int b, int 
         a.val = m.Pn;
         a.dinv = m.dP;
         set_tiles(a, *m.Pcsr);
+        set_sched(a, m.P);
         a.b = b;
         a.X = buf[(j - 1) & 1];
         a.ldx = b;
@@ -225,6 +239,7 @@ static int mass_steps(const Mats<T>& m, int b, int k_M, double lo, double hi, co
         a.val = m.Mr;
         a.dinv = m.dM;
         set_tiles(a, *m.Mcsr);
+        set_sched(a, m.P);
         a.b = b;
         a.X = buf[(j - 1) & 1];
         a.ldx = b;
@@ -312,11 +327,12 @@ int filter_apply_t(nm_problem* P, const nm_filter* f, const T* Y, int64_t ldy, T
 struct MixScratch {
     double *TA, *TB, *W, *S64, *Q64;
     float *w32, *xa, *xb, *xs, *es;
+    float *Th, *Tl;   // double-float split of the block K_eff is applied to
 };
 
 static int get_mix_scratch(nm_problem* P, int b, MixScratch& S) {
     const int64_t n = P->info.n, Np = P->info.Np;
-    const size_t need = (size_t)(3 * n + 2 * Np) * b * sizeof(double) + (size_t)5 * n * b * sizeof(float);
+    const size_t need = (size_t)(3 * n + 2 * Np) * b * sizeof(double) + (size_t)7 * n * b * sizeof(float);
     if (P->ws.bytes < need) {
         P->ws.buf.release();
         NM_TRY(P->ws.buf.alloc(need));
@@ -333,14 +349,16 @@ static int get_mix_scratch(nm_problem* P, int b, MixScratch& S) {
     S.xa = f; f += n * b;
     S.xb = f; f += n * b;
     S.xs = f; f += n * b;
-    S.es = f;
+    S.es = f; f += n * b;
+    S.Th = f; f += n * b;
+    S.Tl = f;
     return NM_OK;
 }
 
 // k steps of float Jacobi-Chebyshev semi-iteration for (A (x) I_R) x = w;
 // w, xa, xb, xout: (R nodes) x b floats with ld b, xout distinct from xa, xb.
-static int cheb32(const DevCSR& A, int R, int b, int k, double lo, double hi, const float* w, float* xa,
-                  float* xb, float* xout, cudaStream_t s) {
+static int cheb32(nm_problem* P, const DevCSR& A, int R, int b, int k, double lo, double hi, const float* w,
+                  float* xa, float* xb, float* xout, cudaStream_t s) {
     const ChebCoef cc(lo, hi);
     const int64_t nodes = A.nrows;
     if (k == 1) return launch_dscale<float>(R, nodes, b, (float)cc.inv_theta, A.dinv32.as<float>(), w, b, xout, b, s);
@@ -356,6 +374,7 @@ static int cheb32(const DevCSR& A, int R, int b, int k, double lo, double hi, co
         a.val = A.val32.as<float>();
         a.dinv = A.dinv32.as<float>();
         set_tiles(a, A);
+        set_sched(a, P);
         a.b = b;
         a.X = buf[(j - 1) & 1];
         a.ldx = b;
@@ -374,20 +393,26 @@ static int cheb32(const DevCSR& A, int R, int b, int k, double lo, double hi, co
 
 // Refined solve: x = P32 w, r = w - A x (double), e = P32 r; leaves x in
 // S.xs and e in S.es (the caller combines them).
-static int mixed_solve(const DevCSR& A, int R, int b, int k, const double* W, int64_t ldw, const MixScratch& S,
-                       cudaStream_t s) {
+static int mixed_solve(nm_problem* P, const DevCSR& A, int R, int b, int k, const double* W, int64_t ldw,
+                       const MixScratch& S, bool df, cudaStream_t s) {
     const int64_t rows = R * A.nrows;
     NM_TRY((launch_convert<double, float>(rows, b, W, ldw, S.w32, b, s)));
-    NM_TRY(cheb32(A, R, b, k, kMassLo, kMassHi, S.w32, S.xa, S.xb, S.xs, s));
-    NM_TRY(launch_resid_mixed(R, A.nrows, A.rowptr.as<int>(), A.col.as<int>(), A.val.as<double>(), W, ldw, S.xs,
-                              S.w32, b, s));
-    return cheb32(A, R, b, k, kMassLo, kMassHi, S.w32, S.xa, S.xb, S.es, s);
+    NM_TRY(cheb32(P, A, R, b, k, kMassLo, kMassHi, S.w32, S.xa, S.xb, S.xs, s));
+    if (df)
+        NM_TRY(launch_resid_df(R, A.nrows, A.rowptr.as<int>(), A.col.as<int>(), A.val32.as<float>(),
+                               A.vlo32.as<float>(), W, ldw, S.xs, S.w32, b, s));
+    else
+        NM_TRY(launch_resid_mixed(R, A.nrows, A.rowptr.as<int>(), A.col.as<int>(), A.val.as<double>(), W, ldw,
+                                  S.xs, S.w32, b, s));
+    return cheb32(P, A, R, b, k, kMassLo, kMassHi, S.w32, S.xa, S.xb, S.es, s);
 }
 
 // W = K_eff X in double with the pressure inverse by a refined solve.
 static int apply_K_mixed(nm_problem* P, const double* X, int64_t ldx, double* W, int64_t ldw, int b, int k_P,
                          const MixScratch& S, cudaStream_t s) {
     Mats<double> m = mats<double>(P);
+    const bool df = P->use_df != 0;
+    if (df) NM_TRY(launch_split(P->info.n, b, X, ldx, S.Th, S.Tl, s));
     Bsr33Args<double> a;
     a.nrows = (int)m.Nu;
     a.rowptr = m.u_rp;
@@ -410,7 +435,7 @@ static int apply_K_mixed(nm_problem* P, const double* X, int64_t ldx, double* W,
         q.Q = S.Q64;
         q.ldq = b;
         NM_TRY(launch_bsr13<double>(q, s));
-        NM_TRY(mixed_solve(P->Pn, 1, b, k_P, S.Q64, b, S, s));
+        NM_TRY(mixed_solve(P, P->Pn, 1, b, k_P, S.Q64, b, S, P->use_df != 0, s));
         CombineArgs c;
         c.rows = m.Np;
         c.b = b;
@@ -424,7 +449,24 @@ static int apply_K_mixed(nm_problem* P, const double* X, int64_t ldx, double* W,
         a.S = S.S64;
         a.lds = b;
     }
-    return launch_bsr33<double>(a, s);
+    if (!df) return launch_bsr33<double>(a, s);
+    Bsr33DfArgs f;
+    f.nrows = a.nrows;
+    f.rowptr = a.rowptr;
+    f.col = a.col;
+    f.vh = P->AG.val32.as<float>();
+    f.vl = P->AG.vlo32.as<float>();
+    f.Xh = S.Th;
+    f.Xl = S.Tl;
+    f.b = b;
+    f.e_rowptr = a.e_rowptr;
+    f.e_col = a.e_col;
+    f.e_val = a.e_val;
+    f.S = a.S;
+    f.lds = a.lds;
+    f.W = W;
+    f.ldw = ldw;
+    return launch_bsr33_df(f, s);
 }
 
 static int filter_apply_mixed(nm_problem* P, const nm_filter* f, const double* Y, int64_t ldy, double* Z,
@@ -435,6 +477,7 @@ static int filter_apply_mixed(nm_problem* P, const nm_filter* f, const double* Y
     if (!(f->e > 0)) return fail(NM_EINVAL, "filter half-width e must be positive");
     if (f->m_lo > 0 || f->m_hi > 0) return fail(NM_EUNSUPPORTED, "mixed mode uses the P2 element bounds");
     NM_TRY(ensure_f32(P, s));
+    if (P->use_df) NM_TRY(ensure_df(P, s));
     const int64_t n = P->info.n;
     MixScratch S;
     NM_TRY(get_mix_scratch(P, b, S));
@@ -450,7 +493,7 @@ static int filter_apply_mixed(nm_problem* P, const nm_filter* f, const double* Y
         NM_TRY(apply_K_mixed(P, cur, b, S.W, b, b, f->k_P, S, s));
         NM_TRY(prof_end(P, s, 1, e0, kl));
         NM_TRY(prof_begin(P, s, &e1));
-        NM_TRY(mixed_solve(P->Mr, 3, b, f->k_M, S.W, b, S, s));
+        NM_TRY(mixed_solve(P, P->Mr, 3, b, f->k_M, S.W, b, S, P->use_df != 0, s));
         CombineArgs c;
         c.rows = n;
         c.b = b;
@@ -480,6 +523,7 @@ int filter_apply_mixed_pub(nm_problem* P, const nm_filter* f, const double* Y, i
 int apply_K_mixed_pub(nm_problem* P, const double* X, int64_t ldx, double* Y, int64_t ldy, int b, int k_P,
                       cudaStream_t s) {
     NM_TRY(ensure_f32(P, s));
+    if (P->use_df) NM_TRY(ensure_df(P, s));
     MixScratch S;
     NM_TRY(get_mix_scratch(P, b, S));
     return apply_K_mixed(P, X, ldx, Y, ldy, b, k_P, S, s);
@@ -488,9 +532,10 @@ int apply_K_mixed_pub(nm_problem* P, const double* X, int64_t ldx, double* Y, in
 int solve_M_mixed_pub(nm_problem* P, int k_M, const double* W, int64_t ldw, double* X, int64_t ldx, int b,
                       cudaStream_t s) {
     NM_TRY(ensure_f32(P, s));
+    if (P->use_df) NM_TRY(ensure_df(P, s));
     MixScratch S;
     NM_TRY(get_mix_scratch(P, b, S));
-    NM_TRY(mixed_solve(P->Mr, 3, b, k_M, W, ldw, S, s));
+    NM_TRY(mixed_solve(P, P->Mr, 3, b, k_M, W, ldw, S, P->use_df != 0, s));
     CombineArgs c;
     c.rows = P->info.n;
     c.b = b;
@@ -1076,6 +1121,10 @@ int lanczos_slice(nm_problem* P, const nm_slice_opts* o, nm_result** out) {
                 }
             if (std::sqrt(r2) <= conv_T * std::max(std::fabs(th[i]), 1.0)) ++nconv;
         }
+        if (o->log_every > 0 && (j + 1) % o->log_every == 0)
+            fprintf(stderr, "[nm] block %d m=%d wanted=%d converged=%d filter %.1fs total %.1fs\n", j + 1, m, nwanted,
+                    nconv, t_filter,
+                    std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
         const bool last = j + 1 == o->max_blocks || !ok;
         if ((nwanted > 0 && nconv == nwanted && (j + 1) % check == 0) || last) {
             NM_TRY(rayleigh_ritz(P, V.as<double>(), ldv, m, lam_lo, lam_hi, nullptr, rr));
@@ -1187,6 +1236,7 @@ int ritz(nm_problem* P, nm_ritz_mode mode, const double* V, int64_t ldv, int m, 
                                      Bd.as<cuDoubleComplex>(), m2, wd.as<double>(), work.as<cuDoubleComplex>(),
                                      lwork, info.as<int>()));
         int h = 0;
+        NM_CUDA(cudaStreamSynchronize(s));
         NM_CUDA(cudaMemcpy(&h, info.p, sizeof(int), cudaMemcpyDeviceToHost));
         if (h != 0) return fail(NM_ENOTCONV, "rotating dense eigensolver failed");
         std::vector<double> w(m2);
@@ -1235,6 +1285,7 @@ int ritz(nm_problem* P, nm_ritz_mode mode, const double* V, int64_t ldv, int m, 
             NM_TRY(apply_cols(P, 1, Ui.as<double>(), k, MUi.as<double>(), k, k, 0, s));
             NM_TRY(apply_cols(P, 2, Ur.as<double>(), k, RUr.as<double>(), k, k, 0, s));
             NM_TRY(apply_cols(P, 2, Ui.as<double>(), k, RUi.as<double>(), k, k, 0, s));
+            NM_CUDA(cudaStreamSynchronize(s));
             std::vector<double> hK[2], hM[2], hRr[2];
             for (int p = 0; p < 2; ++p) {
                 hK[p].resize((size_t)n * k);

@@ -27,7 +27,7 @@ EXPORTS = (
     "nm_apply_K", "nm_apply_M", "nm_solve_M", "nm_apply_R", "nm_set_interval",
     "nm_spectrum_bounds", "nm_filter_design", "nm_filter_apply", "nm_lanczos_slice", "nm_ritz",
     "nm_result_get_info", "nm_result_values", "nm_result_vectors", "nm_result_free",
-    "nm_profile", "nm_profile_read", "nm_kernel_launches",
+    "nm_profile", "nm_profile_read", "nm_kernel_launches", "nm_set_option",
 )
 
 
@@ -64,7 +64,7 @@ class nm_slice_opts(C.Structure):
     _fields_ = [("block", C.c_int32), ("degree", C.c_int32), ("k_M", C.c_int32), ("k_P", C.c_int32),
                 ("max_blocks", C.c_int32), ("check_every", C.c_int32), ("filter_prec", C.c_int32),
                 ("tol", C.c_double), ("seed", C.c_uint64), ("start", C.c_void_p),
-                ("bounds_steps", C.c_int32)]
+                ("bounds_steps", C.c_int32), ("log_every", C.c_int32)]
 
 
 class nm_result_info(C.Structure):
@@ -104,6 +104,7 @@ def _load():
         "nm_result_free": [vp],
         "nm_profile": [vp, i32, i32],
         "nm_profile_read": [vp, i32, C.POINTER(i64), C.POINTER(dbl)],
+        "nm_set_option": [vp, C.c_char_p, i64],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -338,9 +339,9 @@ class Problem:
                                     _prec_of(Y) if prec is None else prec, _stream(stream)), self.ctx.h)
 
     def lanczos_slice(self, block, degree, k_M=0, k_P=0, max_blocks=40, check_every=1, prec=NM_F64,
-                      tol=1e-6, seed=1, start=None, bounds_steps=40, allow_unconverged=False):
+                      tol=1e-6, seed=1, start=None, bounds_steps=40, allow_unconverged=False, log_every=0):
         o = nm_slice_opts(block, degree, k_M, k_P, max_blocks, check_every, prec, tol, seed,
-                          C.c_void_p(start.data_ptr()) if start is not None else None, bounds_steps)
+                          C.c_void_p(start.data_ptr()) if start is not None else None, bounds_steps, log_every)
         h = C.c_void_p()
         rc = _lib.nm_lanczos_slice(self.h, C.byref(o), C.byref(h))
         if rc != NM_OK and not (rc == NM_ENOTCONV and h.value and allow_unconverged):
@@ -356,6 +357,9 @@ class Problem:
         _check(_lib.nm_ritz(self.h, mode, _dptr(V), V.stride(0), m,
                             le.ctypes.data_as(C.c_void_p) if le is not None else None, C.byref(h)), self.ctx.h)
         return Result(self.ctx, h)
+
+    def set_option(self, key, value):
+        _check(_lib.nm_set_option(self.h, key.encode(), int(value)), self.ctx.h)
 
     def profile(self, enable=True, reset=True):
         _check(_lib.nm_profile(self.h, 1 if enable else 0, 1 if reset else 0), self.ctx.h)
