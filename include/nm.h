@@ -176,11 +176,11 @@ int nm_problem_unodes(const nm_problem* prob, int64_t* canon, int64_t* p2, int64
 int nm_problem_export(const nm_problem* prob, int which, int64_t* nrows, int64_t* nnz,
                       int64_t* rowptr, int32_t* col, double* vals);
 
-/* Tuning knobs of a problem (the autotuner's hooks). key "sched": 1
- * (default) runs the semi-iteration SpMMs of blocks 17..64 wide as
- * persistent SM-local kernels (each SM walks its own contiguous range of
- * Morton-ordered rows, so neighbour gathers hit in L1); 0 uses one thread
- * group per row over a plain grid. key "tile_rows": height of the row
+/* Tuning knobs of a problem (the autotuner's hooks). key "sched": 1 runs
+ * the semi-iteration SpMMs of blocks 17..64 wide as persistent SM-local
+ * kernels (each SM walks its own contiguous range of Morton-ordered rows,
+ * so neighbour gathers hit in L1); 0 (default) uses one warp per row over
+ * a plain grid with four gathers in flight per lane. key "tile_rows": height of the row
  * tiles whose gathered operand the float kernels stage in shared memory
  * (0, the default, disables staging; 4..64, power of two); the tiles are
  * rebuilt on the host. key "tile_kernel": 1 or 2, the staged kernel
@@ -191,6 +191,15 @@ int nm_problem_export(const nm_problem* prob, int which, int64_t* nrows, int64_t
  * two floats, error-free products and sums, ~2^-48 relative); 0 runs them
  * in double. NM_EINVAL for an unknown key or value. */
 int nm_set_option(nm_problem* prob, const char* key, int64_t value);
+
+/* Autotuner: times one degree of the filter recurrence (precision prec,
+ * block width b, inner steps k_M) on this problem for every kernel variant
+ * of the options above ("sched", "tile_rows"/"tile_kernel", and for
+ * NM_MIXED "double_float"), keeps the fastest, and reports the time per
+ * column and degree of block widths 16, 32 and 64 with it. All variants
+ * compute the same sums (up to rounding order). report: caller buffer
+ * (may be NULL) for a one-line JSON summary, truncated to report_len. */
+int nm_autotune(nm_problem* prob, int b, nm_prec prec, int k_M, char* report, int report_len);
 
 /* Reference field g' at the internal u-nodes (host out, 3*Nu doubles). */
 int nm_problem_gravity(const nm_problem* prob, double* g);
@@ -244,6 +253,16 @@ int nm_filter_apply(nm_problem* prob, const nm_filter* f, const void* Y, int64_t
  * before every eigenpair in the slice passes tol (the result is still
  * returned). */
 int nm_lanczos_slice(nm_problem* prob, const nm_slice_opts* opts, nm_result** out);
+
+/* Batched slices: nslices slices (lo[i], hi[i] in the given unit, as in
+ * nm_set_interval) solved in lockstep with one filter recurrence per block
+ * step over the concatenated blocks (nslices * block <= 64 columns; the
+ * slices share the spectrum bounds and the Chebyshev map, each keeps its
+ * own coefficients, basis, reorthogonalisation, convergence test and
+ * Rayleigh-Ritz). out: caller array of nslices result pointers.
+ * NM_ENOTCONV if any slice stops at max_blocks (every result is returned). */
+int nm_lanczos_multi(nm_problem* prob, const nm_slice_opts* opts, int nslices, const double* lo, const double* hi,
+                     nm_unit unit, nm_result** out);
 
 /* Rayleigh-Ritz on a caller basis V (device, n x m, row-major, ld ldv,
  * FP64). NM_RITZ_PENCIL: Ritz pairs of (K_eff, M) on span V inside the

@@ -4,6 +4,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "kernels.h"
 #include "nm_internal.h"
@@ -33,10 +34,13 @@ void jackson_step_coeffs(double lam_lo, double lam_hi, double xi, double eta, in
                          double* e);
 int spectrum_bounds(nm_problem* P, int steps, int k_M, uint64_t seed, double* lam_lo, double* lam_hi);
 int lanczos_slice(nm_problem* P, const nm_slice_opts* o, nm_result** out);
+int lanczos_multi(nm_problem* P, const nm_slice_opts* o, int S, const double* lam_lo_in, const double* lam_hi_in,
+                  nm_result** out);
 int ritz(nm_problem* P, nm_ritz_mode mode, const double* V, int64_t ldv, int m, const double* lam_e,
          nm_result** out);
 int profile_read(nm_problem* P, int kind, int64_t* launches, double* ms);
 int set_tile_rows(nm_problem* P, int64_t rows);
+int autotune(nm_problem* P, int b, nm_prec prec, int k_M, std::string* report);
 int profile_set(nm_problem* P, int enable, int reset);
 
 uint64_t launches_so_far();
@@ -227,6 +231,19 @@ int nm_set_option(nm_problem* P, const char* key, int64_t value) {
     return fail(NM_EINVAL, std::string("unknown option: ") + key);
 }
 
+int nm_autotune(nm_problem* P, int b, nm_prec prec, int k_M, char* report, int report_len) {
+    if (!P) return fail(NM_EINVAL, "null problem");
+    CtxScope sc(P->ctx);
+    std::string rep;
+    NM_TRY(autotune(P, b, prec, k_M, &rep));
+    if (report && report_len > 0) {
+        const size_t m = std::min<size_t>(rep.size(), (size_t)report_len - 1);
+        std::memcpy(report, rep.data(), m);
+        report[m] = 0;
+    }
+    return NM_OK;
+}
+
 int nm_problem_gravity(const nm_problem* P, double* g) {
     if (!P || !g) return fail(NM_EINVAL, "null argument");
     CtxScope sc(P->ctx);
@@ -343,6 +360,29 @@ int nm_lanczos_slice(nm_problem* P, const nm_slice_opts* opts, nm_result** out) 
     CtxScope sc(P->ctx);
     *out = nullptr;
     return lanczos_slice(P, opts, out);
+}
+
+int nm_lanczos_multi(nm_problem* P, const nm_slice_opts* opts, int nslices, const double* lo, const double* hi,
+                     nm_unit unit, nm_result** out) {
+    if (!P || !opts || !out || !lo || !hi || nslices < 1) return fail(NM_EINVAL, "bad argument");
+    CtxScope sc(P->ctx);
+    std::vector<double> l(nslices), u(nslices);
+    for (int i = 0; i < nslices; ++i) {
+        out[i] = nullptr;
+        if (!(hi[i] > lo[i]) || !std::isfinite(lo[i]) || !std::isfinite(hi[i]))
+            return fail(NM_EINVAL, "each slice needs finite lo < hi");
+        if (unit == NM_UNIT_OMEGA) {
+            if (hi[i] <= 0) return fail(NM_EINVAL, "omega interval needs hi > 0");
+            l[i] = lo[i] > 0 ? lo[i] * lo[i] : 0.0;
+            u[i] = hi[i] * hi[i];
+        } else if (unit == NM_UNIT_OMEGA2) {
+            l[i] = lo[i];
+            u[i] = hi[i];
+        } else {
+            return fail(NM_EINVAL, "unknown unit");
+        }
+    }
+    return lanczos_multi(P, opts, nslices, l.data(), u.data(), out);
 }
 
 int nm_ritz(nm_problem* P, nm_ritz_mode mode, const double* V, int64_t ldv, int m, const double* lam_e,

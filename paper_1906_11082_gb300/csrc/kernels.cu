@@ -64,7 +64,7 @@ __device__ __forceinline__ void kron_epilogue(const KronArgs<T>& a, int64_t row,
                 const T tp = a.Tp ? a.Tp[r * a.ldtp + c] : T(0);
                 const T tn = a.a1 * (xn - a.cshift * tk) - a.a2 * tp;
                 a.Tn[r * a.ldtn + c] = tn;
-                if (a.Z) a.Z[r * a.ldz + c] += a.gam * tn;
+                if (a.Z) a.Z[r * a.ldz + c] += (a.gam_tab ? (T)a.gam_tab[c / a.gam_group] : a.gam) * tn;
             }
         }
     }
@@ -342,6 +342,91 @@ static int kron_sm_launch(const KronArgs<T>& a, cudaStream_t s) {
     return NM_OK;
 }
 
+// Warp-per-row variant for blocks 17..64 wide (plain grid, 8 rows per
+// CTA): the row's (value, column) pairs are read 32 at a time and consumed
+// four at a time, so each lane keeps 4 R independent gathers in flight and
+// two accumulator sets break the FMA chains.
+template <typename T, int R, int CPT, int MODE>
+__global__ void __launch_bounds__(kThreads) kron_warp_kernel(const KronArgs<T> a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (row >= a.nrows) return;
+    T acc[CPT][R], acc2[CPT][R];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q)
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[q][k] = acc2[q][k] = T(0);
+    const int e0 = __ldg(a.rowptr + row), e1 = __ldg(a.rowptr + row + 1);
+    const int64_t RL = (int64_t)R * a.ldx;
+    for (int base = e0; base < e1; base += 32) {
+        const int e = base + lane;
+        const T vr = e < e1 ? __ldg(a.val + e) : T(0);
+        const int cr = e < e1 ? __ldg(a.col + e) : 0;
+        const int cnt = min(32, e1 - base);
+        int jj = 0;
+        for (; jj + 4 <= cnt; jj += 4) {
+            T v[4];
+            const T* x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                v[u] = __shfl_sync(0xffffffffu, vr, jj + u);
+                x[u] = a.X + RL * __shfl_sync(0xffffffffu, cr, jj + u);
+            }
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                const int c = lane + 32 * q;
+                if (c < a.b) {
+                    T g[4][R];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int k = 0; k < R; ++k) g[u][k] = __ldg(x[u] + k * a.ldx + c);
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        acc[q][k] += v[0] * g[0][k];
+                        acc2[q][k] += v[1] * g[1][k];
+                        acc[q][k] += v[2] * g[2][k];
+                        acc2[q][k] += v[3] * g[3][k];
+                    }
+                }
+            }
+        }
+        for (; jj < cnt; ++jj) {
+            const T v = __shfl_sync(0xffffffffu, vr, jj);
+            const T* xj = a.X + RL * __shfl_sync(0xffffffffu, cr, jj);
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                const int c = lane + 32 * q;
+                if (c < a.b) {
+#pragma unroll
+                    for (int k = 0; k < R; ++k) acc[q][k] += v * __ldg(xj + k * a.ldx + c);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int c = lane + 32 * q;
+        if (c >= a.b) continue;
+#pragma unroll
+        for (int k = 0; k < R; ++k) acc[q][k] += acc2[q][k];
+        kron_epilogue<T, R, MODE>(a, row, c, acc[q]);
+    }
+}
+
+template <typename T, int R, int MODE>
+static int kron_warp_launch(const KronArgs<T>& a, cudaStream_t s) {
+    const int64_t grid = (a.nrows + kThreads / 32 - 1) / (kThreads / 32);
+    if (grid == 0) return NM_OK;
+    if (a.b > 32)
+        kron_warp_kernel<T, R, 2, MODE><<<(unsigned)grid, kThreads, 0, s>>>(a);
+    else
+        kron_warp_kernel<T, R, 1, MODE><<<(unsigned)grid, kThreads, 0, s>>>(a);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
 template <typename T>
 static bool tiled_ok(const KronArgs<T>& a) {
     if (!std::is_same<T, float>::value || !a.tile_uptr || a.ntiles == 0 || a.b != 32 || a.ldx != 32) return false;
@@ -370,6 +455,18 @@ int launch_kron(int R, int mode, const KronArgs<T>& a, cudaStream_t s) {
             if (R == 3 && mode == KRON_CHEB_FILT) return kron_tile_launch<3, KRON_CHEB_FILT>(a, s);
             if (R == 3 && mode == KRON_PLAIN) return kron_tile_launch<3, KRON_PLAIN>(a, s);
             if (R == 1 && mode == KRON_CHEB) return kron_tile_launch<1, KRON_CHEB>(a, s);
+        }
+    }
+    if (a.b >= 17 && a.b <= 64) {
+        if (R == 3) {
+            switch (mode) {
+                case KRON_PLAIN: return kron_warp_launch<T, 3, KRON_PLAIN>(a, s);
+                case KRON_CHEB: return kron_warp_launch<T, 3, KRON_CHEB>(a, s);
+                case KRON_CHEB_FILT: return kron_warp_launch<T, 3, KRON_CHEB_FILT>(a, s);
+                case KRON_CORI: return kron_warp_launch<T, 3, KRON_CORI>(a, s);
+            }
+        } else if (R == 1 && mode == KRON_CHEB) {
+            return kron_warp_launch<T, 1, KRON_CHEB>(a, s);
         }
     }
     const int shift = tpr_shift_for(a.b);
@@ -735,7 +832,7 @@ __global__ void combine_kernel(const CombineArgs a) {
         if (a.Z) {
             const int64_t i = t / a.b;
             const int c = (int)(t - i * a.b);
-            a.Z[i * a.ldz + c] += a.gam * tn;
+            a.Z[i * a.ldz + c] += (a.gam_tab ? a.gam_tab[c / a.gam_group] : a.gam) * tn;
         }
     }
 }
@@ -762,7 +859,7 @@ __device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al,
     const float err = __fadd_rn(__fadd_rn(sh, -__fadd_rn(s, -bp)), __fadd_rn(p, -bp));
     const float lo = __fadd_rn(__fadd_rn(sl, err), t);
     sh = __fadd_rn(s, lo);
-    sl = __fadd_rn(lo, -__fadd_rn(sh, s));
+    sl = __fadd_rn(lo, -__fadd_rn(sh, -s));
 }
 
 __global__ void split_kernel(int64_t rows, int b, const double* X, int64_t ldx, float* Xh, float* Xl) {

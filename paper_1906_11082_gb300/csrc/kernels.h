@@ -33,6 +33,8 @@ struct KronArgs {
     T* Tn = nullptr;        int64_t ldtn = 0;  // FILT next (may alias Tp)
     T* Z = nullptr;         int64_t ldz = 0;   // FILT accumulator (nullptr: none)
     T a1 = 0, cshift = 0, a2 = 0, gam = 0;
+    const double* gam_tab = nullptr;   // FILT: per column group gamma (overrides gam)
+    int gam_group = 1;                 // columns per group
     T sk[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};      // CORI 3x3 (row-major)
     // optional row tiles (see DevCSR): float operands with b = 32 and
     // ldx = 32 then gather through shared memory
@@ -120,6 +122,8 @@ struct CombineArgs {
     double* Z = nullptr;
     int64_t ldz = 0;
     double a1 = 0, cshift = 0, a2 = 0, gam = 0;
+    const double* gam_tab = nullptr;   // per column group gamma (overrides gam)
+    int gam_group = 1;
 };
 int launch_combine(const CombineArgs& a, cudaStream_t s);
 

@@ -135,7 +135,7 @@ struct nm_problem {
     // mixed form: K_eff SpMM and refinement residuals in double-float
     int use_df = 1;
     // SM-local persistent schedule of the semi-iteration kernels
-    int use_sched = 1;
+    int use_sched = 0;
     nm::DevBuf sched;   // int [nreg] region counters
     int nreg = 0;
     // scratch for the filter recurrence

@@ -19,6 +19,11 @@ namespace nm {
 
 int ensure_f32(nm_problem* P, cudaStream_t s);
 int ensure_df(nm_problem* P, cudaStream_t s);
+template <typename T>
+int filter_apply_t(nm_problem* P, const nm_filter* f, const T* Y, int64_t ldy, T* Z, int64_t ldz, int b, cudaStream_t s);
+struct GammaTable;
+static int filter_apply_mixed(nm_problem* P, const nm_filter* f, const double* Y, int64_t ldy, double* Z,
+                              int64_t ldz, int b, cudaStream_t s, const GammaTable* gt = nullptr);
 
 static const double kMassLo = 0.25;
 static const double kMassHi = (19.0 + 15.779733838059499) / 8.0;   // (19 + sqrt(249)) / 8
@@ -219,8 +224,19 @@ static int apply_K_t(nm_problem* P, const T* X, int64_t ldx, T* W, int64_t ldw, 
 // Mass-solve semi-iteration steps 2..k_M starting from x_1 in S.XA and the
 // right-hand side S.W. With filt != nullptr the last step is fused with
 // the outer Chebyshev update; otherwise x_{k_M} is copied to Xout.
+// Per-slice gammas of a batched filter: dev[k * S + g] is gamma_k of the
+// slice owning column group g (group columns wide); host mirrors it.
+struct GammaTable {
+    const double* dev;
+    const double* host;
+    int S;
+    int group;
+};
+
 struct FiltStep {
     double a1, cshift, a2, gam;
+    const double* gam_tab = nullptr;   // device, one gamma per column group
+    int gam_group = 1;
 };
 
 template <typename T>
@@ -262,6 +278,8 @@ static int mass_steps(const Mats<T>& m, int b, int k_M, double lo, double hi, co
             a.cshift = (T)filt->cshift;
             a.a2 = (T)filt->a2;
             a.gam = (T)filt->gam;
+            a.gam_tab = filt->gam_tab;
+            a.gam_group = filt->gam_group;
             NM_TRY(launch_kron<T>(3, KRON_CHEB_FILT, a, s));
         } else if (j == k_M && Xout) {
             a.Xn = Xout;
@@ -277,10 +295,10 @@ static int mass_steps(const Mats<T>& m, int b, int k_M, double lo, double hi, co
 }
 
 template <typename T>
-int filter_apply_t(nm_problem* P, const nm_filter* f, const T* Y, int64_t ldy, T* Z, int64_t ldz,
-                   int b, cudaStream_t s) {
+static int filter_core(nm_problem* P, const nm_filter* f, const T* Y, int64_t ldy, T* Z, int64_t ldz, int b,
+                       const GammaTable* gt, cudaStream_t s) {
     const int d = f->degree;
-    if (d < 0 || !f->gamma) return fail(NM_EINVAL, "filter needs degree >= 0 and gamma");
+    if (d < 0 || (!f->gamma && !gt)) return fail(NM_EINVAL, "filter needs degree >= 0 and gamma");
     if (f->k_M < 2 || (P->info.Np > 0 && f->k_P < 2)) return fail(NM_EINVAL, "k_M and k_P must be >= 2");
     if (!(f->e > 0)) return fail(NM_EINVAL, "filter half-width e must be positive");
     const double mlo = f->m_lo > 0 ? f->m_lo : kMassLo;
@@ -291,7 +309,13 @@ int filter_apply_t(nm_problem* P, const nm_filter* f, const T* Y, int64_t ldy, T
     NM_TRY(get_scratch<T>(P, b, S));
     Mats<T> m = mats<T>(P);
     const ChebCoef cc(mlo, mhi);
-    NM_TRY(launch_scale_copy<T>(n, b, (T)f->gamma[0], Y, ldy, Z, ldz, s));
+    if (gt) {
+        for (int g = 0; g < gt->S; ++g)
+            NM_TRY(launch_scale_copy<T>(n, gt->group, (T)gt->host[g], Y + g * gt->group, ldy, Z + g * gt->group,
+                                        ldz, s));
+    } else {
+        NM_TRY(launch_scale_copy<T>(n, b, (T)f->gamma[0], Y, ldy, Z, ldz, s));
+    }
     if (d == 0) return NM_OK;
     NM_TRY(launch_scale_copy<T>(n, b, (T)1, Y, ldy, S.TA, b, s));
     T* cur = S.TA;   // T_k
@@ -305,7 +329,11 @@ int filter_apply_t(nm_problem* P, const nm_filter* f, const T* Y, int64_t ldy, T
         NM_TRY(prof_begin(P, s, &e1));
         FiltStep fs;
         fs.cshift = f->c;
-        fs.gam = f->gamma[k + 1];
+        fs.gam = gt ? 0.0 : f->gamma[k + 1];
+        if (gt) {
+            fs.gam_tab = gt->dev + (int64_t)(k + 1) * gt->S;
+            fs.gam_group = gt->group;
+        }
         if (k == 0) {
             fs.a1 = 1.0 / f->e;
             fs.a2 = 0.0;
@@ -470,9 +498,9 @@ static int apply_K_mixed(nm_problem* P, const double* X, int64_t ldx, double* W,
 }
 
 static int filter_apply_mixed(nm_problem* P, const nm_filter* f, const double* Y, int64_t ldy, double* Z,
-                              int64_t ldz, int b, cudaStream_t s) {
+                              int64_t ldz, int b, cudaStream_t s, const GammaTable* gt) {
     const int d = f->degree;
-    if (d < 0 || !f->gamma) return fail(NM_EINVAL, "filter needs degree >= 0 and gamma");
+    if (d < 0 || (!f->gamma && !gt)) return fail(NM_EINVAL, "filter needs degree >= 0 and gamma");
     if (f->k_M < 1 || (P->info.Np > 0 && f->k_P < 1)) return fail(NM_EINVAL, "k_M and k_P must be >= 1");
     if (!(f->e > 0)) return fail(NM_EINVAL, "filter half-width e must be positive");
     if (f->m_lo > 0 || f->m_hi > 0) return fail(NM_EUNSUPPORTED, "mixed mode uses the P2 element bounds");
@@ -481,7 +509,13 @@ static int filter_apply_mixed(nm_problem* P, const nm_filter* f, const double* Y
     const int64_t n = P->info.n;
     MixScratch S;
     NM_TRY(get_mix_scratch(P, b, S));
-    NM_TRY(launch_scale_copy<double>(n, b, f->gamma[0], Y, ldy, Z, ldz, s));
+    if (gt) {
+        for (int g = 0; g < gt->S; ++g)
+            NM_TRY(launch_scale_copy<double>(n, gt->group, gt->host[g], Y + g * gt->group, ldy, Z + g * gt->group,
+                                             ldz, s));
+    } else {
+        NM_TRY(launch_scale_copy<double>(n, b, f->gamma[0], Y, ldy, Z, ldz, s));
+    }
     if (d == 0) return NM_OK;
     NM_TRY(launch_scale_copy<double>(n, b, 1.0, Y, ldy, S.TA, b, s));
     double* cur = S.TA;
@@ -507,7 +541,11 @@ static int filter_apply_mixed(nm_problem* P, const nm_filter* f, const double* Y
         c.a1 = (k == 0 ? 1.0 : 2.0) / f->e;
         c.cshift = f->c;
         c.a2 = k == 0 ? 0.0 : 1.0;
-        c.gam = f->gamma[k + 1];
+        c.gam = gt ? 0.0 : f->gamma[k + 1];
+        if (gt) {
+            c.gam_tab = gt->dev + (int64_t)(k + 1) * gt->S;
+            c.gam_group = gt->group;
+        }
         NM_TRY(launch_combine(c, s));
         NM_TRY(prof_end(P, s, 0, e1, 2 * f->k_M + 3));
         std::swap(cur, prev);
@@ -601,6 +639,12 @@ int profile_set(nm_problem* P, int enable, int reset) {
     return NM_OK;
 }
 
+template <typename T>
+int filter_apply_t(nm_problem* P, const nm_filter* f, const T* Y, int64_t ldy, T* Z, int64_t ldz, int b,
+                   cudaStream_t s) {
+    return filter_core<T>(P, f, Y, ldy, Z, ldz, b, nullptr, s);
+}
+
 // ------------------------------------------------------------------ public pieces
 template <typename T>
 int apply_K_pub(nm_problem* P, const T* X, int64_t ldx, T* Y, int64_t ldy, int b, int k_P, cudaStream_t s) {
@@ -676,6 +720,108 @@ template int apply_M_pub<float>(nm_problem*, const float*, int64_t, float*, int6
 template int solve_M_pub<double>(nm_problem*, int, double, double, const double*, int64_t, double*, int64_t, int, cudaStream_t);
 template int solve_M_pub<float>(nm_problem*, int, double, double, const float*, int64_t, float*, int64_t, int, cudaStream_t);
 
+// ------------------------------------------------------------------ autotuner
+int set_tile_rows(nm_problem* P, int64_t rows);
+
+// Device milliseconds of `reps` filter degrees (one filter_apply of degree
+// reps) on the problem's stream.
+static int time_degree(nm_problem* P, int b, nm_prec prec, int k_M, const void* Y, void* Z, int reps, double* ms) {
+    cudaStream_t s = P->ctx->stream;
+    std::vector<double> gamma(reps + 1, 0.5);
+    const double lo = -1.0, hi = 2.0 * (P->bounds_hi > 0 ? P->bounds_hi : 1.0);
+    nm_filter f{reps, gamma.data(), 0.5 * (hi + lo), 0.5 * (hi - lo), k_M, k_M, 0.0, 0.0};
+    auto run = [&]() -> int {
+        if (prec == NM_F64) return filter_apply_t<double>(P, &f, (const double*)Y, b, (double*)Z, b, b, s);
+        if (prec == NM_F32) return filter_apply_t<float>(P, &f, (const float*)Y, b, (float*)Z, b, b, s);
+        return filter_apply_mixed(P, &f, (const double*)Y, b, (double*)Z, b, b, s);
+    };
+    NM_TRY(run());   // warm-up (also allocates the scratch)
+    cudaEvent_t e0, e1;
+    NM_CUDA(cudaEventCreate(&e0));
+    NM_CUDA(cudaEventCreate(&e1));
+    NM_CUDA(cudaEventRecord(e0, s));
+    int rc = run();
+    NM_CUDA(cudaEventRecord(e1, s));
+    NM_CUDA(cudaEventSynchronize(e1));
+    float x = 0.f;
+    cudaEventElapsedTime(&x, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = x;
+    return rc;
+}
+
+int autotune(nm_problem* P, int b, nm_prec prec, int k_M, std::string* report) {
+    if (b < 1 || b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
+    if (k_M < 2) k_M = prec == NM_F64 ? 38 : (prec == NM_MIXED ? 20 : 28);
+    cudaStream_t s = P->ctx->stream;
+    if (prec != NM_F64) NM_TRY(ensure_f32(P, s));
+    if (prec == NM_MIXED) NM_TRY(ensure_df(P, s));
+    const int64_t n = P->info.n;
+    const size_t es = prec == NM_F32 ? sizeof(float) : sizeof(double);
+    DevBuf Y, Z;
+    NM_TRY(Y.alloc((size_t)n * 64 * es));
+    NM_TRY(Z.alloc((size_t)n * 64 * es));
+    NM_CUDA(cudaMemsetAsync(Y.p, 0, (size_t)n * 64 * es, s));
+    if (prec == NM_F32) {
+        // float start block: 64 columns of Gaussians drawn in double and narrowed
+        NM_TRY(launch_philox_normal(n * 32, 7, Z.as<double>(), s));
+        NM_TRY((launch_convert<double, float>(n, 32, Z.as<double>(), 32, Y.as<float>(), 32, s)));
+        NM_TRY((launch_convert<double, float>(n, 32, Z.as<double>(), 32, Y.as<float>() + n * 32, 32, s)));
+    } else {
+        NM_TRY(launch_philox_normal(n * 64, 7, Y.as<double>(), s));
+    }
+    struct Cfg { int sched, tile, tk, df; };
+    std::vector<Cfg> cfgs;
+    for (int sched : {0, 1})
+        for (int df : (prec == NM_MIXED ? std::vector<int>{1, 0} : std::vector<int>{P->use_df}))
+            cfgs.push_back({sched, 0, 2, df});
+    if (prec != NM_F64 && b == 32) {
+        cfgs.push_back({0, 16, 2, prec == NM_MIXED ? 1 : P->use_df});
+        cfgs.push_back({0, 32, 2, prec == NM_MIXED ? 1 : P->use_df});
+    }
+    const int reps = 2;
+    double best = 1e300;
+    Cfg bestc = cfgs[0];
+    std::string rep = "{\"b\": " + std::to_string(b) + ", \"variants\": [";
+    for (size_t i = 0; i < cfgs.size(); ++i) {
+        const Cfg& c = cfgs[i];
+        P->use_sched = c.sched;
+        P->use_df = c.df;
+        NM_TRY(set_tile_rows(P, c.tile));
+        if (c.tile) P->Mr.tile_kernel = P->Pn.tile_kernel = c.tk;
+        double ms = 0;
+        NM_TRY(time_degree(P, b, prec, k_M, Y.p, Z.p, reps, &ms));
+        ms /= reps;
+        char buf[160];
+        snprintf(buf, sizeof buf, "%s{\"sched\": %d, \"tile_rows\": %d, \"double_float\": %d, \"ms_per_degree\": %.4f}",
+                 i ? ", " : "", c.sched, c.tile, c.df, ms);
+        rep += buf;
+        if (ms < best) {
+            best = ms;
+            bestc = c;
+        }
+    }
+    P->use_sched = bestc.sched;
+    P->use_df = bestc.df;
+    NM_TRY(set_tile_rows(P, bestc.tile));
+    if (bestc.tile) P->Mr.tile_kernel = P->Pn.tile_kernel = bestc.tk;
+    rep += "], \"chosen\": {\"sched\": " + std::to_string(bestc.sched) + ", \"tile_rows\": " +
+           std::to_string(bestc.tile) + ", \"double_float\": " + std::to_string(bestc.df) + "}, \"us_per_column_degree\": {";
+    int first = 1;
+    for (int bb : {16, 32, 64}) {
+        double ms = 0;
+        NM_TRY(time_degree(P, bb, prec, k_M, Y.p, Z.p, reps, &ms));
+        char buf[64];
+        snprintf(buf, sizeof buf, "%s\"%d\": %.3f", first ? "" : ", ", bb, 1e3 * ms / reps / bb);
+        rep += buf;
+        first = 0;
+    }
+    rep += "}}";
+    *report = rep;
+    return NM_OK;
+}
+
 // ------------------------------------------------------------------ filter design
 void jackson_step_coeffs(double lam_lo, double lam_hi, double xi, double eta, int d, double* gamma,
                          double* c, double* e) {
@@ -737,11 +883,14 @@ struct OpBuf {
 };
 
 // W = p(B) V_j (prec selects the filter arithmetic); V_j, W FP64 row-major
-static int filter_block(nm_problem* P, const nm_filter* f, const double* Vj, int64_t ldv, double* W,
-                        int b, nm_prec prec, DevBuf& fin, DevBuf& fout, cudaStream_t s) {
+static int filter_block(nm_problem* P, nm_prec prec, int d, double c, double e, int k_M, int k_P, const double* Y,
+                        int64_t ldy, double* W, int64_t ldw, const GammaTable* gt, DevBuf& fin, DevBuf& fout,
+                        cudaStream_t s) {
     const int64_t n = P->info.n;
-    if (prec == NM_F64) return filter_apply_t<double>(P, f, Vj, ldv, W, b, b, s);
-    if (prec == NM_MIXED) return filter_apply_mixed(P, f, Vj, ldv, W, b, b, s);
+    const int b = gt->S * gt->group;
+    nm_filter f{d, nullptr, c, e, k_M, k_P, 0.0, 0.0};
+    if (prec == NM_F64) return filter_core<double>(P, &f, Y, ldy, W, ldw, b, gt, s);
+    if (prec == NM_MIXED) return filter_apply_mixed(P, &f, Y, ldy, W, ldw, b, s, gt);
     NM_TRY(ensure_f32(P, s));
     if (fin.bytes < (size_t)n * b * sizeof(float)) {
         fin.release();
@@ -749,9 +898,9 @@ static int filter_block(nm_problem* P, const nm_filter* f, const double* Vj, int
         NM_TRY(fin.alloc((size_t)n * b * sizeof(float)));
         NM_TRY(fout.alloc((size_t)n * b * sizeof(float)));
     }
-    NM_TRY((launch_convert<double, float>(n, b, Vj, ldv, fin.as<float>(), b, s)));
-    NM_TRY(filter_apply_t<float>(P, f, fin.as<float>(), b, fout.as<float>(), b, b, s));
-    return launch_convert<float, double>(n, b, fout.as<float>(), b, W, b, s);
+    NM_TRY((launch_convert<double, float>(n, b, Y, ldy, fin.as<float>(), b, s)));
+    NM_TRY(filter_core<float>(P, &f, fin.as<float>(), b, fout.as<float>(), b, b, gt, s));
+    return launch_convert<float, double>(n, b, fout.as<float>(), b, W, ldw, s);
 }
 
 // Apply K_eff (FP64, effectively exact Schur term) or M to m columns of a
@@ -1009,13 +1158,32 @@ int spectrum_bounds(nm_problem* P, int steps, int k_M, uint64_t seed, double* la
 }
 
 // ------------------------------------------------------------------ Lanczos
-int lanczos_slice(nm_problem* P, const nm_slice_opts* o, nm_result** out) {
+// One slice's filtered block Lanczos state (basis, projected matrix, filter).
+struct SliceState {
+    double lam_lo = 0, lam_hi = 0, tau = 0;
+    std::vector<double> gamma;
+    DevBuf V, MW, C, H, G;
+    std::vector<double> Tfull;
+    int blocks = 0, m_used = 0;
+    bool active = true, converged = false, ok = true;
+    RRResult rr;
+    nm_result* R = nullptr;
+};
+
+// Filtered block Lanczos for S slices in lockstep (S = 1: nm_lanczos_slice).
+// The slices share the spectrum bounds, hence the Chebyshev map (c, e) and
+// the recurrence; their current blocks are filtered together as one block
+// of S b columns with a per-slice gamma in the accumulation. Each slice has
+// its own M-orthonormal basis, two-pass CGS, Cholesky-QR, projected matrix,
+// convergence test and Rayleigh-Ritz, and leaves the batch when done.
+int lanczos_multi(nm_problem* P, const nm_slice_opts* o, int S, const double* lam_lo_in, const double* lam_hi_in,
+                  nm_result** out) {
     auto t_start = std::chrono::steady_clock::now();
     nm_ctx* ctx = P->ctx;
     cudaStream_t s = ctx->stream;
-    if (!P->have_interval) return fail(NM_EINVAL, "call nm_set_interval first");
     const int b = o->block;
-    if (b < 1 || b > 64) return fail(NM_EINVAL, "block must be in 1..64");
+    if (S < 1) return fail(NM_EINVAL, "need at least one slice");
+    if (b < 1 || (int64_t)b * S > 64) return fail(NM_EINVAL, "slices x block must be in 1..64");
     if (o->degree < 1) return fail(NM_EINVAL, "degree must be >= 1");
     if (o->max_blocks < 2) return fail(NM_EINVAL, "max_blocks must be >= 2");
     const int k_M = o->k_M > 0 ? o->k_M : 57;
@@ -1023,142 +1191,171 @@ int lanczos_slice(nm_problem* P, const nm_slice_opts* o, nm_result** out) {
     const double tol = o->tol > 0 ? o->tol : 1e-6;
     const int check = o->check_every > 0 ? o->check_every : 1;
     const int64_t n = P->info.n;
+    const int d = o->degree;
     double blo, bhi;
     NM_TRY(spectrum_bounds(P, o->bounds_steps > 0 ? o->bounds_steps : 40, k_M, o->seed + 1, &blo, &bhi));
-    const double lam_lo = P->lo <= 0 ? -1e-8 * bhi : P->lo;
-    const double lam_hi = P->hi;
-    std::vector<double> gamma(o->degree + 1);
-    double c, e;
-    jackson_step_coeffs(blo, bhi, lam_lo, lam_hi, o->degree, gamma.data(), &c, &e);
-    const double pa = cheb_sum(gamma, (lam_lo - c) / e), pb = cheb_sum(gamma, (lam_hi - c) / e);
-    const double tau = lam_lo > blo ? 0.8 * std::min(pa, pb) : 0.8 * pb;
-    nm_filter f{o->degree, gamma.data(), c, e, k_M, k_P, 0.0, 0.0};
-    // Ritz values of the filtered operator count as converged below this
-    // relative residual estimate; a float filter carries rounding noise of
-    // ~d * 6e-8 in every filtered vector, so it cannot go below ~1e-5.
     const double conv_T = o->filter_prec == NM_F32 ? 1e-5 : 1e-8;
-
     const int mmax = b * o->max_blocks;
     const int ldv = mmax + b;
-    DevBuf V, W, MW, C, H, G, fin, fout;
-    NM_TRY(V.alloc((size_t)n * ldv * sizeof(double)));
-    NM_TRY(W.alloc((size_t)n * b * sizeof(double)));
-    NM_TRY(MW.alloc((size_t)n * b * sizeof(double)));
-    NM_TRY(C.alloc((size_t)ldv * b * sizeof(double)));
-    NM_TRY(H.alloc((size_t)ldv * b * sizeof(double)));
-    NM_TRY(G.alloc((size_t)b * b * sizeof(double)));
-    // start block
-    if (o->start) {
-        NM_TRY(launch_scale_copy<double>(n, b, 1.0, o->start, b, V.as<double>(), ldv, s));
-    } else {
-        NM_TRY(launch_philox_normal(n * b, o->seed, W.as<double>(), s));
-        NM_TRY(launch_scale_copy<double>(n, b, 1.0, W.as<double>(), b, V.as<double>(), ldv, s));
+    std::vector<SliceState> st(S);
+    double c = 0, e = 0;
+    for (int q = 0; q < S; ++q) {
+        SliceState& z = st[q];
+        if (!(lam_hi_in[q] > lam_lo_in[q])) return fail(NM_EINVAL, "slice needs lo < hi");
+        z.lam_lo = lam_lo_in[q] <= 0 ? -1e-8 * bhi : lam_lo_in[q];
+        z.lam_hi = lam_hi_in[q];
+        z.gamma.resize(d + 1);
+        jackson_step_coeffs(blo, bhi, z.lam_lo, z.lam_hi, d, z.gamma.data(), &c, &e);
+        const double pa = cheb_sum(z.gamma, (z.lam_lo - c) / e), pb = cheb_sum(z.gamma, (z.lam_hi - c) / e);
+        z.tau = z.lam_lo > blo ? 0.8 * std::min(pa, pb) : 0.8 * pb;
+        NM_TRY(z.V.alloc((size_t)n * ldv * sizeof(double)));
+        NM_TRY(z.MW.alloc((size_t)n * b * sizeof(double)));
+        NM_TRY(z.C.alloc((size_t)ldv * b * sizeof(double)));
+        NM_TRY(z.H.alloc((size_t)ldv * b * sizeof(double)));
+        NM_TRY(z.G.alloc((size_t)b * b * sizeof(double)));
+        z.Tfull.assign((size_t)mmax * mmax, 0.0);
+        // start block: the caller's (same for every slice) or Philox with a per-slice stream
+        if (o->start) {
+            NM_TRY(launch_scale_copy<double>(n, b, 1.0, o->start, b, z.V.as<double>(), ldv, s));
+        } else {
+            NM_TRY(launch_philox_normal(n * b, o->seed + 0x9E3779B97F4A7C15ull * q, z.MW.as<double>(), s));
+            NM_TRY(launch_scale_copy<double>(n, b, 1.0, z.MW.as<double>(), b, z.V.as<double>(), ldv, s));
+        }
+        int ok = 1;
+        NM_TRY(m_orth(P, z.V.as<double>(), ldv, b, z.MW.as<double>(), z.G.as<double>(), &ok, s));
+        if (!ok) return fail(NM_ENOTCONV, "start block is rank deficient in the M inner product");
     }
-    int ok = 1;
-    NM_TRY(m_orth(P, V.as<double>(), ldv, b, MW.as<double>(), G.as<double>(), &ok, s));
-    if (!ok) return fail(NM_ENOTCONV, "start block is rank deficient in the M inner product");
-    std::vector<double> Tfull((size_t)mmax * mmax, 0.0);
+    DevBuf Ycat, Wcat, gtab, fin, fout;
+    NM_TRY(Ycat.alloc((size_t)n * S * b * sizeof(double)));
+    NM_TRY(Wcat.alloc((size_t)n * S * b * sizeof(double)));
+    NM_TRY(gtab.alloc((size_t)(d + 1) * S * sizeof(double)));
     double t_filter = 0.0;
-    int blocks = 0;
-    RRResult rr;
-    bool converged = false;
-    int m_used = 0;
     for (int j = 0; j < o->max_blocks; ++j) {
-        const int m = (j + 1) * b;   // basis columns including V_j
-        double* Vj = V.as<double>() + (int64_t)j * b;
+        std::vector<int> act;
+        for (int q = 0; q < S; ++q)
+            if (st[q].active) act.push_back(q);
+        if (act.empty()) break;
+        const int Sa = (int)act.size();
+        const int B = Sa * b;
+        const int m = (j + 1) * b;
+        // gamma table of the active slices and their concatenated current blocks
+        std::vector<double> gt((size_t)(d + 1) * Sa), g0(Sa);
+        for (int g = 0; g < Sa; ++g) {
+            for (int k = 0; k <= d; ++k) gt[(size_t)k * Sa + g] = st[act[g]].gamma[k];
+            NM_TRY(launch_scale_copy<double>(n, b, 1.0, st[act[g]].V.as<double>() + (int64_t)j * b, ldv,
+                                             Ycat.as<double>() + g * b, B, s));
+        }
+        NM_CUDA(cudaMemcpyAsync(gtab.p, gt.data(), gt.size() * sizeof(double), cudaMemcpyHostToDevice, s));
         NM_CUDA(cudaStreamSynchronize(s));
         auto t0 = std::chrono::steady_clock::now();
-        NM_TRY(filter_block(P, &f, Vj, ldv, W.as<double>(), b, o->filter_prec, fin, fout, s));
+        GammaTable table{gtab.as<double>(), gt.data(), Sa, b};
+        NM_TRY(filter_block(P, o->filter_prec, d, c, e, k_M, k_P, Ycat.as<double>(), B, Wcat.as<double>(), B, &table,
+                            fin, fout, s));
         NM_CUDA(cudaStreamSynchronize(s));
         t_filter += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        // CGS2 against the whole basis in the M inner product
-        NM_CUDA(cudaMemsetAsync(H.p, 0, (size_t)m * b * sizeof(double), s));
-        for (int pass = 0; pass < 2; ++pass) {
-            NM_TRY(apply_M_pub<double>(P, W.as<double>(), b, MW.as<double>(), b, b, KRON_PLAIN, nullptr, s));
-            NM_TRY(gemm_VtW(ctx, n, m, b, V.as<double>(), ldv, MW.as<double>(), b, C.as<double>(), 0.0));
-            NM_TRY(gemm_WmVC(ctx, n, m, b, -1.0, V.as<double>(), ldv, C.as<double>(), m, W.as<double>(), b));
-            const double one = 1.0;
-            NM_CUBLAS(cublasDaxpy(ctx->cublas, m * b, &one, C.as<double>(), 1, H.as<double>(), 1));
-        }
-        std::vector<double> hH((size_t)m * b);
-        NM_CUDA(cudaMemcpyAsync(hH.data(), H.p, hH.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-        // new block
-        double* Vn = V.as<double>() + (int64_t)(j + 1) * b;
-        NM_TRY(launch_scale_copy<double>(n, b, 1.0, W.as<double>(), b, Vn, ldv, s));
-        NM_TRY(m_orth(P, Vn, ldv, b, MW.as<double>(), G.as<double>(), &ok, s));
-        std::vector<double> hR((size_t)b * b);
-        NM_CUDA(cudaMemcpy(hR.data(), G.p, hR.size() * sizeof(double), cudaMemcpyDeviceToHost));
-        for (int cc = 0; cc < b; ++cc)
-            for (int r = 0; r < m; ++r) Tfull[(size_t)r + (size_t)(j * b + cc) * mmax] = hH[(size_t)r + (size_t)cc * m];
-        blocks = j + 1;
-        m_used = m;
-        // projected filtered operator: symmetrised T (m x m), eig on the device
-        std::vector<double> Tm((size_t)m * m);
-        for (int r = 0; r < m; ++r)
-            for (int cc = 0; cc < m; ++cc) {
-                const double a = r <= cc ? Tfull[(size_t)r + (size_t)cc * mmax] : Tfull[(size_t)cc + (size_t)r * mmax];
-                Tm[(size_t)r + (size_t)cc * m] = a;
+        for (int g = 0; g < Sa; ++g) {
+            SliceState& z = st[act[g]];
+            double* W = Wcat.as<double>() + g * b;   // ld B
+            // CGS2 against the slice's basis in the M inner product
+            NM_CUDA(cudaMemsetAsync(z.H.p, 0, (size_t)m * b * sizeof(double), s));
+            for (int pass = 0; pass < 2; ++pass) {
+                NM_TRY(apply_M_pub<double>(P, W, B, z.MW.as<double>(), b, b, KRON_PLAIN, nullptr, s));
+                NM_TRY(gemm_VtW(ctx, n, m, b, z.V.as<double>(), ldv, z.MW.as<double>(), b, z.C.as<double>(), 0.0));
+                NM_TRY(gemm_WmVC(ctx, n, m, b, -1.0, z.V.as<double>(), ldv, z.C.as<double>(), m, W, B));
+                const double one = 1.0;
+                NM_CUBLAS(cublasDaxpy(ctx->cublas, m * b, &one, z.C.as<double>(), 1, z.H.as<double>(), 1));
             }
-        DevBuf Td, wd;
-        NM_TRY(Td.alloc(Tm.size() * sizeof(double)));
-        NM_TRY(wd.alloc(m * sizeof(double)));
-        NM_CUDA(cudaMemcpy(Td.p, Tm.data(), Tm.size() * sizeof(double), cudaMemcpyHostToDevice));
-        NM_TRY(dense_eig(ctx, m, Td.as<double>(), nullptr, wd.as<double>()));
-        std::vector<double> th(m), Sv((size_t)m * m);
-        NM_CUDA(cudaMemcpy(th.data(), wd.p, m * sizeof(double), cudaMemcpyDeviceToHost));
-        NM_CUDA(cudaMemcpy(Sv.data(), Td.p, Sv.size() * sizeof(double), cudaMemcpyDeviceToHost));
-        int nwanted = 0, nconv = 0;
-        for (int i = 0; i < m; ++i) {
-            if (th[i] < tau) continue;
-            ++nwanted;
-            // residual estimate || R_{j+1} S[last b rows, i] ||, R upper triangular (col-major)
-            double r2 = 0;
-            if (ok)
-                for (int r = 0; r < b; ++r) {
-                    double v = 0;
-                    for (int q = r; q < b; ++q) v += hR[(size_t)r + (size_t)q * b] * Sv[(size_t)(m - b + q) + (size_t)i * m];
-                    r2 += v * v;
+            std::vector<double> hH((size_t)m * b);
+            NM_CUDA(cudaMemcpyAsync(hH.data(), z.H.p, hH.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+            double* Vn = z.V.as<double>() + (int64_t)(j + 1) * b;
+            NM_TRY(launch_scale_copy<double>(n, b, 1.0, W, B, Vn, ldv, s));
+            int ok = 1;
+            NM_TRY(m_orth(P, Vn, ldv, b, z.MW.as<double>(), z.G.as<double>(), &ok, s));
+            z.ok = ok != 0;
+            std::vector<double> hR((size_t)b * b);
+            NM_CUDA(cudaMemcpy(hR.data(), z.G.p, hR.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            for (int cc = 0; cc < b; ++cc)
+                for (int r = 0; r < m; ++r)
+                    z.Tfull[(size_t)r + (size_t)(j * b + cc) * mmax] = hH[(size_t)r + (size_t)cc * m];
+            z.blocks = j + 1;
+            z.m_used = m;
+            std::vector<double> Tm((size_t)m * m);
+            for (int r = 0; r < m; ++r)
+                for (int cc = 0; cc < m; ++cc)
+                    Tm[(size_t)r + (size_t)cc * m] = r <= cc ? z.Tfull[(size_t)r + (size_t)cc * mmax]
+                                                             : z.Tfull[(size_t)cc + (size_t)r * mmax];
+            DevBuf Td, wd;
+            NM_TRY(Td.alloc(Tm.size() * sizeof(double)));
+            NM_TRY(wd.alloc(m * sizeof(double)));
+            NM_CUDA(cudaMemcpy(Td.p, Tm.data(), Tm.size() * sizeof(double), cudaMemcpyHostToDevice));
+            NM_TRY(dense_eig(ctx, m, Td.as<double>(), nullptr, wd.as<double>()));
+            std::vector<double> th(m), Sv((size_t)m * m);
+            NM_CUDA(cudaMemcpy(th.data(), wd.p, m * sizeof(double), cudaMemcpyDeviceToHost));
+            NM_CUDA(cudaMemcpy(Sv.data(), Td.p, Sv.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            int nwanted = 0, nconv = 0;
+            for (int i = 0; i < m; ++i) {
+                if (th[i] < z.tau) continue;
+                ++nwanted;
+                double r2 = 0;
+                if (ok)
+                    for (int r = 0; r < b; ++r) {
+                        double v = 0;
+                        for (int qq = r; qq < b; ++qq)
+                            v += hR[(size_t)r + (size_t)qq * b] * Sv[(size_t)(m - b + qq) + (size_t)i * m];
+                        r2 += v * v;
+                    }
+                if (std::sqrt(r2) <= conv_T * std::max(std::fabs(th[i]), 1.0)) ++nconv;
+            }
+            if (o->log_every > 0 && (j + 1) % o->log_every == 0)
+                fprintf(stderr, "[nm] slice %d block %d m=%d wanted=%d converged=%d filter %.1fs total %.1fs\n", act[g],
+                        j + 1, m, nwanted, nconv, t_filter,
+                        std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+            const bool last = j + 1 == o->max_blocks || !ok;
+            if ((nwanted > 0 && nconv == nwanted && (j + 1) % check == 0) || last) {
+                if (!z.R) {
+                    z.R = new (std::nothrow) nm_result();
+                    if (!z.R) return fail(NM_ENOMEM, "host allocation failed");
                 }
-            if (std::sqrt(r2) <= conv_T * std::max(std::fabs(th[i]), 1.0)) ++nconv;
-        }
-        if (o->log_every > 0 && (j + 1) % o->log_every == 0)
-            fprintf(stderr, "[nm] block %d m=%d wanted=%d converged=%d filter %.1fs total %.1fs\n", j + 1, m, nwanted,
-                    nconv, t_filter,
-                    std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
-        const bool last = j + 1 == o->max_blocks || !ok;
-        if ((nwanted > 0 && nconv == nwanted && (j + 1) % check == 0) || last) {
-            NM_TRY(rayleigh_ritz(P, V.as<double>(), ldv, m, lam_lo, lam_hi, nullptr, rr));
-            bool all = rr.k > 0;
-            for (double r : rr.res) all = all && r <= tol;
-            if (all || last) {
-                converged = all;
-                break;
+                NM_TRY(rayleigh_ritz(P, z.V.as<double>(), ldv, m, z.lam_lo, z.lam_hi, &z.R->X, z.rr));
+                bool all = z.rr.k > 0;
+                for (double r : z.rr.res) all = all && r <= tol;
+                if (all || last) {
+                    z.converged = all;
+                    z.active = false;
+                }
             }
         }
     }
-    nm_result* R = new (std::nothrow) nm_result();
-    if (!R) return fail(NM_ENOMEM, "host allocation failed");
-    int rc = rayleigh_ritz(P, V.as<double>(), ldv, m_used, lam_lo, lam_hi, &R->X, rr);
-    if (rc != NM_OK) {
-        delete R;
-        return rc;
+    int rc = NM_OK;
+    for (int q = 0; q < S; ++q) {
+        SliceState& z = st[q];
+        if (!z.R) {
+            z.R = new (std::nothrow) nm_result();
+            if (!z.R) return fail(NM_ENOMEM, "host allocation failed");
+            NM_TRY(rayleigh_ritz(P, z.V.as<double>(), ldv, z.m_used, z.lam_lo, z.lam_hi, &z.R->X, z.rr));
+        }
+        nm_result* R = z.R;
+        R->lambda = z.rr.lam;
+        R->resid = z.rr.res;
+        R->info.k = z.rr.k;
+        R->info.n = n;
+        R->info.blocks = z.blocks;
+        R->info.m = z.m_used;
+        R->info.filter_applications = (int64_t)z.blocks * b;
+        R->info.lam_lo = blo;
+        R->info.lam_hi = bhi;
+        R->info.seconds_filter = t_filter;
+        R->info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+        out[q] = R;
+        if (!z.converged) rc = NM_ENOTCONV;
     }
-    R->lambda = rr.lam;
-    R->resid = rr.res;
-    R->info.k = rr.k;
-    R->info.n = n;
-    R->info.blocks = blocks;
-    R->info.m = m_used;
-    R->info.filter_applications = (int64_t)blocks * b;
-    R->info.lam_lo = blo;
-    R->info.lam_hi = bhi;
-    R->info.seconds_filter = t_filter;
-    R->info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-    *out = R;
-    bool all = rr.k > 0;
-    for (double r : rr.res) all = all && r <= tol;
-    if (!converged && !all) return fail(NM_ENOTCONV, "slice did not converge within max_blocks");
+    if (rc != NM_OK) return fail(rc, "a slice did not converge within max_blocks");
     return NM_OK;
+}
+
+int lanczos_slice(nm_problem* P, const nm_slice_opts* o, nm_result** out) {
+    if (!P->have_interval) return fail(NM_EINVAL, "call nm_set_interval first");
+    return lanczos_multi(P, o, 1, &P->lo, &P->hi, out);
 }
 
 // ------------------------------------------------------------------ Ritz entry

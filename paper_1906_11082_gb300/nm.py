@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -27,7 +28,8 @@ EXPORTS = (
     "nm_apply_K", "nm_apply_M", "nm_solve_M", "nm_apply_R", "nm_set_interval",
     "nm_spectrum_bounds", "nm_filter_design", "nm_filter_apply", "nm_lanczos_slice", "nm_ritz",
     "nm_result_get_info", "nm_result_values", "nm_result_vectors", "nm_result_free",
-    "nm_profile", "nm_profile_read", "nm_kernel_launches", "nm_set_option",
+    "nm_profile", "nm_profile_read", "nm_kernel_launches", "nm_set_option", "nm_autotune",
+    "nm_lanczos_multi",
 )
 
 
@@ -105,6 +107,8 @@ def _load():
         "nm_profile": [vp, i32, i32],
         "nm_profile_read": [vp, i32, C.POINTER(i64), C.POINTER(dbl)],
         "nm_set_option": [vp, C.c_char_p, i64],
+        "nm_autotune": [vp, i32, i32, i32, C.c_char_p, i32],
+        "nm_lanczos_multi": [vp, C.POINTER(nm_slice_opts), i32, vp, vp, i32, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -166,14 +170,23 @@ def _ld(t, b):
 
 
 class Context:
+    """An nm_ctx. Problems and results created under it are freed before it
+    (the C ABI requires children to go first)."""
+
     def __init__(self, device=0):
         h = C.c_void_p()
         _check(_lib.nm_ctx_create(device, C.byref(h)))
         self.h = h
         self.device = device
+        self._children = weakref.WeakSet()
+
+    def _adopt(self, obj):
+        self._children.add(obj)
 
     def close(self):
         if self.h:
+            for ch in list(self._children):
+                ch.free()
             _lib.nm_ctx_destroy(self.h)
             self.h = None
 
@@ -188,6 +201,7 @@ class Result:
     def __init__(self, ctx, h):
         self.ctx = ctx
         self.h = h
+        ctx._adopt(self)
         info = nm_result_info()
         _check(_lib.nm_result_get_info(h, C.byref(info)), ctx.h)
         self.info = {k: getattr(info, k) for k, _ in nm_result_info._fields_}
@@ -212,7 +226,8 @@ class Result:
 
     def free(self):
         if self.h:
-            _lib.nm_result_free(self.h)
+            if self.ctx.h:
+                _lib.nm_result_free(self.h)
             self.h = None
 
     def __del__(self):
@@ -270,6 +285,7 @@ class Problem:
         h = C.c_void_p()
         _check(_lib.nm_assemble(ctx.h, C.byref(m), C.byref(md), C.byref(h)), ctx.h)
         self.h = h
+        ctx._adopt(self)
         info = nm_problem_info()
         _check(_lib.nm_problem_get_info(h, C.byref(info)), ctx.h)
         self.info = {k: getattr(info, k) for k, _ in nm_problem_info._fields_}
@@ -350,6 +366,25 @@ class Problem:
             _check(rc, self.ctx.h)
         return Result(self.ctx, h)
 
+    def lanczos_multi(self, slices, unit=NM_UNIT_OMEGA, block=16, degree=100, k_M=0, k_P=0, max_blocks=40,
+                      check_every=1, prec=NM_F64, tol=1e-6, seed=1, bounds_steps=40, allow_unconverged=False,
+                      log_every=0):
+        """Solve several slices [(lo, hi), ...] in lockstep; returns a list of Results."""
+        S = len(slices)
+        lo = np.ascontiguousarray([s[0] for s in slices], np.float64)
+        hi = np.ascontiguousarray([s[1] for s in slices], np.float64)
+        o = nm_slice_opts(block, degree, k_M, k_P, max_blocks, check_every, prec, tol, seed, None, bounds_steps,
+                          log_every)
+        hs = (C.c_void_p * S)()
+        rc = _lib.nm_lanczos_multi(self.h, C.byref(o), S, lo.ctypes.data_as(C.c_void_p),
+                                   hi.ctypes.data_as(C.c_void_p), unit, C.cast(hs, C.c_void_p))
+        res = [Result(self.ctx, C.c_void_p(h)) for h in hs if h]
+        if rc != NM_OK and not (rc == NM_ENOTCONV and allow_unconverged and len(res) == S):
+            for r in res:
+                r.free()
+            _check(rc, self.ctx.h)
+        return res
+
     def ritz(self, V, mode=NM_RITZ_PENCIL, lam_e=None):
         m = V.shape[1]
         le = None if lam_e is None else np.ascontiguousarray(lam_e, np.float64)
@@ -360,6 +395,13 @@ class Problem:
 
     def set_option(self, key, value):
         _check(_lib.nm_set_option(self.h, key.encode(), int(value)), self.ctx.h)
+
+    def autotune(self, b=32, prec=None, k_M=0):
+        """Pick the fastest kernel variant for this problem; returns the report."""
+        import json
+        buf = C.create_string_buffer(4096)
+        _check(_lib.nm_autotune(self.h, b, NM_MIXED if prec is None else prec, k_M, buf, len(buf)), self.ctx.h)
+        return json.loads(buf.value.decode())
 
     def profile(self, enable=True, reset=True):
         _check(_lib.nm_profile(self.h, 1 if enable else 0, 1 if reset else 0), self.ctx.h)
@@ -372,7 +414,8 @@ class Problem:
 
     def free(self):
         if getattr(self, "h", None):
-            _lib.nm_problem_free(self.h)
+            if self.ctx.h:
+                _lib.nm_problem_free(self.h)
             self.h = None
 
     def __del__(self):

@@ -395,3 +395,42 @@ def test_tile_options_agree(nm, planet):
         P.set_option("tile_rows", 3)
     with pytest.raises(nm.NMError):
         P.set_option("no_such_option", 1)
+
+
+def test_autotune_report_and_results(nm, planet):
+    """The autotuner times the kernel variants on the problem, keeps the
+    fastest, and the results stay those of the oracle."""
+    mesh, model, S, P = planet
+    rep = P.autotune(b=8, prec=nm.NM_MIXED, k_M=20)
+    assert {"variants", "chosen", "us_per_column_degree"} <= set(rep)
+    assert len(rep["variants"]) >= 4 and all(v["ms_per_degree"] > 0 for v in rep["variants"])
+    Wc = np.random.default_rng(21).standard_normal((S.n, 6))
+    X = torch.empty((S.n, 6), dtype=torch.float64, device=DEV)
+    P.solve_M(_dev(to_internal(P, Wc)), X, k_M=20, prec=nm.NM_MIXED)
+    ref = filtlan.refined_solve(S.M, 1.0 / S.M.diagonal(), Wc, 20)
+    assert rel_err(to_canonical(P, _host(X)), ref) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_lanczos_multi_matches_single_slices(nm, ball, prec):
+    """Two slices batched through one filter recurrence give each slice's
+    dense-oracle eigenpairs (the slices share bounds and Chebyshev map)."""
+    w, S, P = ball
+    K, M = eig.pencil_dense(S)
+    lam = eig.all_eigs(K, M)[0]
+    slices = [(0.0, 2.7), (2.7, 3.0)]
+    res = P.lanczos_multi(slices, block=8, degree=100, k_M=40 if prec == "f64" else 20,
+                          k_P=40 if prec == "f64" else 20, max_blocks=16, seed=4,
+                          prec=nm.NM_F64 if prec == "f64" else nm.NM_MIXED)
+    assert len(res) == 2
+    for (lo, hi), r in zip(slices, res):
+        l = -1e-8 * lam[-1] if lo == 0 else lo * lo
+        ref = lam[(lam >= l) & (lam <= hi * hi)]
+        _check_slice(r, ref, lam[-1])
+
+
+def test_lanczos_multi_rejects_too_wide(nm, ball):
+    w, S, P = ball
+    with pytest.raises(nm.NMError) as e:
+        P.lanczos_multi([(0.0, 1.0)] * 5, block=16)
+    assert e.value.code == nm.NM_EINVAL
