@@ -365,12 +365,12 @@ def run_ours(args):
     tfl = mflops / avg_launch_s / 1e12 if ml else None
     if args.prec == "f64" and tfl is not None and tfl / FP64_PEAK_TFLOPS > gbs / peak_hbm:
         roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "kron_kernel<double,3,CHEB>",
+                "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "kron_warp_kernel<double,3,1,CHEB>",
                 "peak_source": "GB300 FP64 nominal (152 SM x 2 FMA/clk x 2.05 GHz)"}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": peak_hbm, "unit": "GB/s",
                 "frac": (gbs / peak_hbm) if gbs else None, "traffic": None,
-                "kernel": "kron_kernel<double,3,CHEB>" if s == 8 else "kron_tile_kernel<3,CHEB> (float)",
+                "kernel": "kron_warp_kernel<double,3,1,CHEB>" if s == 8 else "kron_warp_kernel<float,3,1,CHEB>",
                 "peak_source": f"{peak_src} copy bandwidth"}
     roof["bytes_per_launch"] = mbytes
     roof["flops_per_launch"] = mflops

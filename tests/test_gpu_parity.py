@@ -352,7 +352,9 @@ def test_invalid_block_width(nm, ball):
 
 def test_double_float_matches_double(nm, planet):
     """The mixed form's double-float SpMMs agree with the double ones to
-    about 2^-48 per term (relative to the largest output entry)."""
+    about 2^-48 per term; the float semi-iterations downstream then carry
+    their own rounding (~6e-8 x the 1e-4-size refinement residual), so the
+    outputs agree to ~1e-11 relative to the largest entry."""
     mesh, model, S, P = planet
     Xc = np.random.default_rng(12).standard_normal((S.n, 8))
     X = _dev(to_internal(P, Xc))
@@ -362,12 +364,12 @@ def test_double_float_matches_double(nm, planet):
         P.apply_K(X, Y0, k_P=20, prec=nm.NM_MIXED)
         P.set_option("double_float", 1)
         P.apply_K(X, Y1, k_P=20, prec=nm.NM_MIXED)
-        assert rel_err(_host(Y1), _host(Y0)) <= 1e-13
+        assert rel_err(_host(Y1), _host(Y0)) <= 2e-11
         P.set_option("double_float", 0)
         P.solve_M(X, Y0, 20, prec=nm.NM_MIXED)
         P.set_option("double_float", 1)
         P.solve_M(X, Y1, 20, prec=nm.NM_MIXED)
-        assert rel_err(_host(Y1), _host(Y0)) <= 1e-13
+        assert rel_err(_host(Y1), _host(Y0)) <= 2e-11
     finally:
         P.set_option("double_float", 1)
 
