@@ -247,6 +247,34 @@ int nm_filter_design(double lam_lo, double lam_hi, double xi, double eta, int de
 int nm_filter_apply(nm_problem* prob, const nm_filter* f, const void* Y, int64_t ldy, void* Z,
                     int64_t ldz, int b, nm_prec prec, void* stream);
 
+/* ---- filter application without device allocation -------------------------
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot call cudaMalloc: a host whose device memory is handed out by
+ * another allocator (a framework's pool that has already reserved the free
+ * HBM), a serving loop that cannot afford the device synchronisation of
+ * cudaMalloc / cudaFree, or a host that must know its full device footprint
+ * when the library loads.
+ *
+ * Computes exactly what nm_filter_apply does with prec = NM_F64 (same
+ * kernels in the same order): Z = p(B) Y, Y and Z device arrays of doubles,
+ * row-major n x b with leading dimensions ldy, ldz >= b, owned by the
+ * caller. The recurrence scratch, (5 n + 3 Np) * b * 8 bytes, lives in a
+ * file-scope device array of NM_STATIC_SCRATCH_BYTES; the call allocates
+ * no device memory (no cudaMalloc, cudaFree or allocating library call).
+ *  - Sizes whose scratch exceeds NM_STATIC_SCRATCH_BYTES are rejected with
+ *    NM_EINVAL and a message giving the bytes needed; nothing is launched.
+ *  - Every GPU on which the call runs holds the array until process exit.
+ *  - All calls on one device share the array, which keeps the last call's
+ *    contents (each call clears the bytes it uses on its stream before
+ *    the recurrence). Calls whose kernels overlap on the GPU (different
+ *    streams, threads, contexts or problems) race on it: serialise them.
+ *  - The first call on a device looks up the array's device address with
+ *    cudaGetSymbolAddress; make that first call before any stream capture.
+ *  - Not recorded by nm_profile. Other errors as nm_filter_apply. */
+#define NM_STATIC_SCRATCH_BYTES (16u << 20)
+int nm_filter_apply_static(nm_problem* prob, const nm_filter* f, const double* Y, int64_t ldy, double* Z,
+                           int64_t ldz, int b, void* stream);
+
 /* Filtered block Lanczos for every eigenpair with lambda in the interval
  * set by nm_set_interval (Sec. 6.2), followed by an FP64 Rayleigh-Ritz of
  * the pencil and FP64 residuals. NM_ENOTCONV if max_blocks is reached

@@ -711,6 +711,60 @@ int solve_M_pub(nm_problem* P, int k_M, double lo, double hi, const T* W, int64_
     return mass_steps<T>(m, b, k_M, mlo, mhi, S, nullptr, nullptr, nullptr, nullptr, nullptr, 0, X, ldx, s);
 }
 
+// ------------------------------------------------------------------ caller-supplied scratch
+// Bytes of scratch the FP64 filter recurrence uses for b columns: five n x b
+// blocks (T_k, T_{k-1}, K_eff T_k, two mass-solve iterates) and three Np x b
+// blocks (E_G^T X and two pressure iterates), the layout get_scratch uses.
+size_t filter_scratch_bytes(const nm_problem* P, int b) {
+    return (size_t)(5 * P->info.n + 3 * P->info.Np) * (size_t)b * sizeof(double);
+}
+
+// The FP64 filter recurrence of Sec. 5 (Z = sum_k gamma_k T_k(B) Y) on
+// scratch the caller hands in: at least filter_scratch_bytes(P, b) bytes,
+// 256-byte aligned. Performs no device allocation and records no profile
+// regions; launches the same kernels in the same order as the FP64 branch
+// of nm_filter_apply.
+int filter_apply_on(nm_problem* P, const nm_filter* f, const double* Y, int64_t ldy, double* Z, int64_t ldz,
+                    int b, double* scratch, cudaStream_t s) {
+    const int d = f->degree;
+    if (d < 0 || !f->gamma) return fail(NM_EINVAL, "filter needs degree >= 0 and gamma");
+    if (f->k_M < 2 || (P->info.Np > 0 && f->k_P < 2)) return fail(NM_EINVAL, "k_M and k_P must be >= 2");
+    if (!(f->e > 0)) return fail(NM_EINVAL, "filter half-width e must be positive");
+    const double mlo = f->m_lo > 0 ? f->m_lo : kMassLo;
+    const double mhi = f->m_hi > 0 ? f->m_hi : kMassHi;
+    if (!(mhi > mlo)) return fail(NM_EINVAL, "mass bounds need m_hi > m_lo > 0");
+    const int64_t n = P->info.n, Np = P->info.Np;
+    Scratch<double> S;
+    double* p = scratch;
+    S.TA = p; p += n * b;
+    S.TB = p; p += n * b;
+    S.W = p; p += n * b;
+    S.XA = p; p += n * b;
+    S.XB = p; p += n * b;
+    S.Q = p; p += Np * b;
+    S.PA = p; p += Np * b;
+    S.PB = p;
+    Mats<double> m = mats<double>(P);
+    const ChebCoef cc(mlo, mhi);
+    NM_TRY(launch_scale_copy<double>(n, b, f->gamma[0], Y, ldy, Z, ldz, s));
+    if (d == 0) return NM_OK;
+    NM_TRY(launch_scale_copy<double>(n, b, 1.0, Y, ldy, S.TA, b, s));
+    double* cur = S.TA;   // T_k
+    double* prev = S.TB;  // T_{k-1}, overwritten by T_{k+1}
+    for (int k = 0; k < d; ++k) {
+        NM_TRY(apply_K_t<double>(P, cur, b, S.W, b, b, f->k_P, S, S.XA, cc.inv_theta, s));
+        FiltStep fs;
+        fs.cshift = f->c;
+        fs.gam = f->gamma[k + 1];
+        fs.a1 = (k == 0 ? 1.0 : 2.0) / f->e;
+        fs.a2 = k == 0 ? 0.0 : 1.0;
+        NM_TRY(mass_steps<double>(m, b, f->k_M, mlo, mhi, S, &fs, cur, k == 0 ? nullptr : prev, prev, Z, ldz,
+                                  nullptr, 0, s));
+        std::swap(cur, prev);
+    }
+    return NM_OK;
+}
+
 template int filter_apply_t<double>(nm_problem*, const nm_filter*, const double*, int64_t, double*, int64_t, int, cudaStream_t);
 template int filter_apply_t<float>(nm_problem*, const nm_filter*, const float*, int64_t, float*, int64_t, int, cudaStream_t);
 template int apply_K_pub<double>(nm_problem*, const double*, int64_t, double*, int64_t, int, int, cudaStream_t);

@@ -21,6 +21,7 @@ NM_F64, NM_F32, NM_MIXED = 0, 1, 2
 NM_UNIT_OMEGA, NM_UNIT_OMEGA2 = 0, 1
 NM_RITZ_PENCIL, NM_RITZ_ROTATING = 0, 1
 NM_GRAVITY, NM_CENTRIFUGAL = 1, 2
+NM_STATIC_SCRATCH_BYTES = 16 << 20     # size of the static scratch of nm_filter_apply_static
 
 EXPORTS = (
     "nm_ctx_create", "nm_ctx_destroy", "nm_last_error", "nm_assemble", "nm_problem_free",
@@ -29,7 +30,7 @@ EXPORTS = (
     "nm_spectrum_bounds", "nm_filter_design", "nm_filter_apply", "nm_lanczos_slice", "nm_ritz",
     "nm_result_get_info", "nm_result_values", "nm_result_vectors", "nm_result_free",
     "nm_profile", "nm_profile_read", "nm_kernel_launches", "nm_set_option", "nm_autotune",
-    "nm_lanczos_multi",
+    "nm_lanczos_multi", "nm_filter_apply_static",
 )
 
 
@@ -109,6 +110,7 @@ def _load():
         "nm_set_option": [vp, C.c_char_p, i64],
         "nm_autotune": [vp, i32, i32, i32, C.c_char_p, i32],
         "nm_lanczos_multi": [vp, C.POINTER(nm_slice_opts), i32, vp, vp, i32, vp],
+        "nm_filter_apply_static": [vp, C.POINTER(nm_filter), vp, i64, vp, i64, i32, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -353,6 +355,15 @@ class Problem:
         b = Y.shape[1]
         _check(_lib.nm_filter_apply(self.h, C.byref(f), _dptr(Y), _ld(Y, b), _dptr(Z), _ld(Z, b), b,
                                     _prec_of(Y) if prec is None else prec, _stream(stream)), self.ctx.h)
+
+    def filter_apply_static(self, gamma, c, e, k_M, Y, Z, k_P=None, m_lo=0.0, m_hi=0.0, stream=None):
+        """FP64 filter application with the library's fixed-size static
+        scratch (no device allocation); Y, Z float64 device tensors."""
+        g = np.ascontiguousarray(gamma, np.float64)
+        f = nm_filter(len(g) - 1, _hp(g, C.c_double), c, e, k_M, k_M if k_P is None else k_P, m_lo, m_hi)
+        b = Y.shape[1]
+        _check(_lib.nm_filter_apply_static(self.h, C.byref(f), _dptr(Y), _ld(Y, b), _dptr(Z), _ld(Z, b), b,
+                                           _stream(stream)), self.ctx.h)
 
     def lanczos_slice(self, block, degree, k_M=0, k_P=0, max_blocks=40, check_every=1, prec=NM_F64,
                       tol=1e-6, seed=1, start=None, bounds_steps=40, allow_unconverged=False, log_every=0):
