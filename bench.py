@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--k-m", type=int, default=0)
     ap.add_argument("--profile-case", action="store_true",
                     help="one short mixed filter application on the full matrices (for ncu captures)")
+    ap.add_argument("--chunk", type=int, default=None,
+                    help="chunked row schedule of the semi-iteration SpMMs (threads per CTA; 0 = off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -232,6 +234,8 @@ def run_ours(args):
     w = workload(args.h)
     ctx = nm.Context(local)
     P = nm.Problem(ctx, w.mesh, w.model)
+    if args.chunk is not None:
+        P.set_option("chunk", args.chunk)
     lo, hi = SLICES_OMEGA[rank % len(SLICES_OMEGA)]
     P.set_interval(lo, hi)
     prec = {"f64": nm.NM_F64, "f32": nm.NM_F32, "mixed": nm.NM_MIXED}[args.prec]

@@ -176,11 +176,21 @@ int nm_problem_unodes(const nm_problem* prob, int64_t* canon, int64_t* p2, int64
 int nm_problem_export(const nm_problem* prob, int which, int64_t* nrows, int64_t* nnz,
                       int64_t* rowptr, int32_t* col, double* vals);
 
-/* Tuning knobs of a problem (the autotuner's hooks). key "sched": 1 runs
- * the semi-iteration SpMMs of blocks 17..64 wide as persistent SM-local
- * kernels (each SM walks its own contiguous range of Morton-ordered rows,
- * so neighbour gathers hit in L1); 0 (default) uses one warp per row over
- * a plain grid with four gathers in flight per lane. key "tile_rows": height of the row
+/* Tuning knobs of a problem (the autotuner's hooks). key "sched": 1 gives
+ * the semi-iteration SpMMs of blocks 17..64 wide an SM-local row order
+ * (each SM walks its own contiguous range of Morton-ordered rows, so
+ * neighbour gathers hit in L1): the vectorised kernel below takes its row
+ * blocks in that order, the others run as persistent SM-local kernels;
+ * 0 (default) uses one warp per row over a plain grid. key "chunk": 256,
+ * 512 or 1024 runs those SpMMs one warp per row with each CTA sweeping its
+ * own contiguous range of rows in a single wave (CTA size = the value, L1
+ * preferred over shared memory); 0 (default) turns it off; it takes
+ * precedence over the other schedules. key "vec": 1 (default) runs the float semi-iteration SpMMs
+ * of blocks exactly 32 wide with ld = 32 with 16-byte vectorised gathers
+ * (each row split over four groups of eight lanes), 0 with one 4-byte
+ * gather per lane and component; key "vec_threads" (256 default, 512,
+ * 1024) sets their CTA size, i.e. how many consecutive rows share an SM's
+ * L1. key "tile_rows": height of the row
  * tiles whose gathered operand the float kernels stage in shared memory
  * (0, the default, disables staging; 4..64, power of two); the tiles are
  * rebuilt on the host. key "tile_kernel": 1 or 2, the staged kernel
@@ -194,7 +204,7 @@ int nm_set_option(nm_problem* prob, const char* key, int64_t value);
 
 /* Autotuner: times one degree of the filter recurrence (precision prec,
  * block width b, inner steps k_M) on this problem for every kernel variant
- * of the options above ("sched", "tile_rows"/"tile_kernel", and for
+ * of the options above ("sched", "chunk", "vec", "tile_rows"/"tile_kernel", and for
  * NM_MIXED "double_float"), keeps the fastest, and reports the time per
  * column and degree of block widths 16, 32 and 64 with it. All variants
  * compute the same sums (up to rounding order). report: caller buffer

@@ -218,6 +218,22 @@ int nm_set_option(nm_problem* P, const char* key, int64_t value) {
         P->use_sched = (int)value;
         return NM_OK;
     }
+    if (std::string(key) == "vec") {
+        if (value != 0 && value != 1) return fail(NM_EINVAL, "vec must be 0 or 1");
+        P->use_vec = (int)value;
+        return NM_OK;
+    }
+    if (std::string(key) == "vec_threads") {
+        if (value != 256 && value != 512 && value != 1024) return fail(NM_EINVAL, "vec_threads must be 256, 512 or 1024");
+        P->vec_threads = (int)value;
+        return NM_OK;
+    }
+    if (std::string(key) == "chunk") {
+        if (value != 0 && value != 256 && value != 512 && value != 1024)
+            return fail(NM_EINVAL, "chunk must be 0, 256, 512 or 1024");
+        P->use_chunk = (int)value;
+        return NM_OK;
+    }
     if (std::string(key) == "double_float") {
         if (value != 0 && value != 1) return fail(NM_EINVAL, "double_float must be 0 or 1");
         P->use_df = (int)value;

@@ -347,10 +347,7 @@ static int kron_sm_launch(const KronArgs<T>& a, cudaStream_t s) {
 // four at a time, so each lane keeps 4 R independent gathers in flight and
 // two accumulator sets break the FMA chains.
 template <typename T, int R, int CPT, int MODE>
-__global__ void __launch_bounds__(kThreads) kron_warp_kernel(const KronArgs<T> a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t row = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-    if (row >= a.nrows) return;
+__device__ __forceinline__ void warp_row(const KronArgs<T>& a, const int64_t row, const int lane) {
     T acc[CPT][R], acc2[CPT][R];
 #pragma unroll
     for (int q = 0; q < CPT; ++q)
@@ -414,6 +411,232 @@ __global__ void __launch_bounds__(kThreads) kron_warp_kernel(const KronArgs<T> a
     }
 }
 
+
+template <typename T, int R, int CPT, int MODE>
+__global__ void __launch_bounds__(kThreads) kron_warp_kernel(const KronArgs<T> a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (row >= a.nrows) return;
+    warp_row<T, R, CPT, MODE>(a, row, lane);
+}
+
+// Chunked warp-per-row variant: CTA c owns the contiguous row range
+// [N c / G, N (c + 1) / G) of the Morton-ordered rows and its warps sweep
+// it together (warp w takes rows r0 + w, r0 + w + W, ...), so the
+// neighbour records of consecutive windows of W rows are re-read from L1
+// instead of L2. One wave: G = SMs x resident CTAs, L1 preferred over
+// shared memory.
+template <typename T, int R, int CPT, int MODE>
+__global__ void __launch_bounds__(1024) kron_chunk_kernel(const KronArgs<T> a) {
+    const int lane = threadIdx.x & 31;
+    const int W = blockDim.x >> 5;
+    const int64_t r0 = (int64_t)a.nrows * blockIdx.x / gridDim.x;
+    const int64_t r1 = (int64_t)a.nrows * (blockIdx.x + 1) / gridDim.x;
+    for (int64_t row = r0 + (threadIdx.x >> 5); row < r1; row += W) warp_row<T, R, CPT, MODE>(a, row, lane);
+}
+
+// Vectorised warp-per-row variant for float blocks exactly 32 columns wide
+// and stored densely (ldx = 32, 16-byte aligned), the width of the
+// benchmark's Lanczos block. The warp splits into four groups of eight
+// lanes; group g takes the row's stored entries g, g + 4, g + 8, ... and
+// lane q of the group reads columns 4q..4q+3 of the R components of that
+// neighbour with R 16-byte loads, so one group fetches a whole neighbour
+// record (R x 32 floats) in R instructions and all 32 lanes stay busy.
+// Two entries per group are in flight per trip. The four partial sums are
+// combined by butterfly shuffles and lane c then takes column c for the
+// shared epilogue.
+template <int R, int MODE, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) kron_v4_kernel(const KronArgs<float> a) {
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 3, q = lane & 7;
+    int64_t blk = blockIdx.x;
+    if (a.sched) {
+        // SM-local order: the CTA takes the next row block of its SM's own
+        // contiguous region (then of the following regions once that is
+        // used up), so the CTAs resident on one SM work on neighbouring
+        // Morton rows and share their gathered records in L1. The grid has
+        // exactly one CTA per row block, so every block is taken once.
+        __shared__ int64_t s_blk;
+        if (threadIdx.x == 0) {
+            unsigned smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            const int64_t nblk = gridDim.x;
+            s_blk = -1;
+            for (int k = 0; k < a.nreg; ++k) {
+                const int reg = (int)((smid + k) % (unsigned)a.nreg);
+                const int64_t b0 = nblk * reg / a.nreg, b1 = nblk * (reg + 1) / a.nreg;
+                const int64_t take = atomicAdd(a.sched + reg, 1);
+                if (take < b1 - b0) {
+                    s_blk = b0 + take;
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        blk = s_blk;
+        if (blk < 0) return;
+    }
+    const int64_t row = blk * (NT / 32) + (threadIdx.x >> 5);
+    if (row >= a.nrows) return;
+    float4 acc[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int e0 = __ldg(a.rowptr + row), e1 = __ldg(a.rowptr + row + 1);
+    // The semi-iteration epilogue's own-row operands do not depend on the
+    // gather: issue their loads now so their DRAM latency overlaps it.
+    constexpr bool kCheb = MODE == KRON_CHEB || MODE == KRON_CHEB_FILT;
+    float pw[R], pxk[R], pxp[R], ptk[R], ptp[R];
+    float pd = 0.f;
+    if (kCheb) {
+        pd = a.dinv[row];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int64_t r = R * row + k;
+            // streamed once per step: evict-first, so the gathered block
+            // keeps its L2 lines
+            pxk[k] = a.X[r * a.ldx + lane];
+            pw[k] = __ldcs(a.W + r * a.ldw + lane);
+            pxp[k] = a.Xp ? __ldcs(a.Xp + r * a.ldp + lane) : 0.f;
+            if (MODE == KRON_CHEB_FILT) {
+                ptk[k] = __ldcs(a.Tk + r * a.ldtk + lane);
+                ptp[k] = a.Tp ? __ldcs(a.Tp + r * a.ldtp + lane) : 0.f;
+            }
+        }
+    }
+    const float4* xb = reinterpret_cast<const float4*>(a.X) + q;
+    int e = e0 + g;
+    for (; e + 4 < e1; e += 8) {
+        const int j0 = __ldg(a.col + e), j1 = __ldg(a.col + e + 4);
+        const float v0 = __ldg(a.val + e), v1 = __ldg(a.val + e + 4);
+        const float4* p0 = xb + (int64_t)j0 * (8 * R);
+        const float4* p1 = xb + (int64_t)j1 * (8 * R);
+        float4 x0[R], x1[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            x0[k] = __ldg(p0 + 8 * k);
+            x1[k] = __ldg(p1 + 8 * k);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            acc[k].x += v0 * x0[k].x;
+            acc[k].y += v0 * x0[k].y;
+            acc[k].z += v0 * x0[k].z;
+            acc[k].w += v0 * x0[k].w;
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            acc[k].x += v1 * x1[k].x;
+            acc[k].y += v1 * x1[k].y;
+            acc[k].z += v1 * x1[k].z;
+            acc[k].w += v1 * x1[k].w;
+        }
+    }
+    if (e < e1) {
+        const int j0 = __ldg(a.col + e);
+        const float v0 = __ldg(a.val + e);
+        const float4* p0 = xb + (int64_t)j0 * (8 * R);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const float4 x0 = __ldg(p0 + 8 * k);
+            acc[k].x += v0 * x0.x;
+            acc[k].y += v0 * x0.y;
+            acc[k].z += v0 * x0.z;
+            acc[k].w += v0 * x0.w;
+        }
+    }
+    // lanes q, q + 8, q + 16, q + 24 hold partial sums of the same columns
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+#pragma unroll
+        for (int m = 8; m <= 16; m *= 2) {
+            acc[k].x += __shfl_xor_sync(0xffffffffu, acc[k].x, m);
+            acc[k].y += __shfl_xor_sync(0xffffffffu, acc[k].y, m);
+            acc[k].z += __shfl_xor_sync(0xffffffffu, acc[k].z, m);
+            acc[k].w += __shfl_xor_sync(0xffffffffu, acc[k].w, m);
+        }
+    }
+    // column c = lane lives in element (c & 3) of lane c >> 2
+    const int src = lane >> 2, sel = lane & 3;
+    float out[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const float t0 = __shfl_sync(0xffffffffu, acc[k].x, src);
+        const float t1 = __shfl_sync(0xffffffffu, acc[k].y, src);
+        const float t2 = __shfl_sync(0xffffffffu, acc[k].z, src);
+        const float t3 = __shfl_sync(0xffffffffu, acc[k].w, src);
+        out[k] = sel == 0 ? t0 : (sel == 1 ? t1 : (sel == 2 ? t2 : t3));
+    }
+    if (!kCheb) {
+        kron_epilogue<float, R, MODE>(a, row, lane, out);
+        return;
+    }
+    // same arithmetic as kron_epilogue, on the preloaded operands
+    const float d = pd * a.inv_theta;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int64_t r = R * row + k;
+        const float xn = pxp[k] + a.om * (pxk[k] - pxp[k] + d * (pw[k] - out[k]));
+        if (MODE == KRON_CHEB) {
+            a.Xn[r * a.ldn + lane] = xn;
+        } else {
+            const float tn = a.a1 * (xn - a.cshift * ptk[k]) - a.a2 * ptp[k];
+            a.Tn[r * a.ldtn + lane] = tn;
+            if (a.Z) a.Z[r * a.ldz + lane] += (a.gam_tab ? (float)a.gam_tab[lane / a.gam_group] : a.gam) * tn;
+        }
+    }
+}
+
+template <int R, int MODE>
+static int kron_v4_launch(const KronArgs<float>& a, cudaStream_t s) {
+    // one row per warp; larger CTAs keep more consecutive (Morton-near)
+    // rows, whose neighbour sets overlap, on one SM's L1
+    const int nt = a.vec_threads == 512 || a.vec_threads == 1024 ? a.vec_threads : 256;
+    const int64_t grid = (a.nrows + nt / 32 - 1) / (nt / 32);
+    if (grid == 0) return NM_OK;
+    if (a.sched) NM_CUDA(cudaMemsetAsync(a.sched, 0, a.nreg * sizeof(int), s));
+    if (nt == 1024)
+        kron_v4_kernel<R, MODE, 1024><<<(unsigned)grid, 1024, 0, s>>>(a);
+    else if (nt == 512)
+        kron_v4_kernel<R, MODE, 512><<<(unsigned)grid, 512, 0, s>>>(a);
+    else
+        kron_v4_kernel<R, MODE, 256><<<(unsigned)grid, 256, 0, s>>>(a);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+template <typename T>
+static bool v4_ok(const KronArgs<T>& a) {
+    return std::is_same<T, float>::value && a.vec && a.b == 32 && a.ldx == 32 && ((uintptr_t)a.X & 15) == 0;
+}
+
+template <typename T, int R, int CPT, int MODE>
+static int kron_chunk_launch_t(const KronArgs<T>& a, cudaStream_t s) {
+    // grid per (instantiation, CTA size), found once per process
+    static int grid[3] = {0, 0, 0};
+    const int nt = a.chunk;
+    const int slot = nt == 256 ? 0 : (nt == 512 ? 1 : 2);
+    if (grid[slot] == 0) {
+        int dev = 0, sms = 0, per = 0;
+        NM_CUDA(cudaGetDevice(&dev));
+        NM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        NM_CUDA(cudaFuncSetAttribute(kron_chunk_kernel<T, R, CPT, MODE>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        NM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kron_chunk_kernel<T, R, CPT, MODE>, nt, 0));
+        grid[slot] = sms * (per > 0 ? per : 1);
+    }
+    kron_chunk_kernel<T, R, CPT, MODE><<<(unsigned)grid[slot], (unsigned)nt, 0, s>>>(a);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+template <typename T, int R, int MODE>
+static int kron_chunk_launch(const KronArgs<T>& a, cudaStream_t s) {
+    if (a.nrows == 0) return NM_OK;
+    return a.b > 32 ? kron_chunk_launch_t<T, R, 2, MODE>(a, s) : kron_chunk_launch_t<T, R, 1, MODE>(a, s);
+}
+
 template <typename T, int R, int MODE>
 static int kron_warp_launch(const KronArgs<T>& a, cudaStream_t s) {
     const int64_t grid = (a.nrows + kThreads / 32 - 1) / (kThreads / 32);
@@ -437,6 +660,20 @@ static bool tiled_ok(const KronArgs<T>& a) {
 template <typename T>
 int launch_kron(int R, int mode, const KronArgs<T>& a, cudaStream_t s) {
     if (a.b < 1 || a.b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
+    if constexpr (std::is_same<T, float>::value) {
+        if (v4_ok(a) && !a.chunk) {
+            if (R == 3) {
+                switch (mode) {
+                    case KRON_PLAIN: return kron_v4_launch<3, KRON_PLAIN>(a, s);
+                    case KRON_CHEB: return kron_v4_launch<3, KRON_CHEB>(a, s);
+                    case KRON_CHEB_FILT: return kron_v4_launch<3, KRON_CHEB_FILT>(a, s);
+                    case KRON_CORI: return kron_v4_launch<3, KRON_CORI>(a, s);
+                }
+            } else if (R == 1 && mode == KRON_CHEB) {
+                return kron_v4_launch<1, KRON_CHEB>(a, s);
+            }
+        }
+    }
     if (a.sched && a.nreg > 0 && a.b >= 17 && a.b <= 64) {
         if (R == 3) {
             switch (mode) {
@@ -447,6 +684,18 @@ int launch_kron(int R, int mode, const KronArgs<T>& a, cudaStream_t s) {
             }
         } else if (R == 1 && mode == KRON_CHEB) {
             return kron_sm_launch<T, 1, KRON_CHEB>(a, s);
+        }
+    }
+    if (a.chunk && a.b >= 17 && a.b <= 64) {
+        if (R == 3) {
+            switch (mode) {
+                case KRON_PLAIN: return kron_chunk_launch<T, 3, KRON_PLAIN>(a, s);
+                case KRON_CHEB: return kron_chunk_launch<T, 3, KRON_CHEB>(a, s);
+                case KRON_CHEB_FILT: return kron_chunk_launch<T, 3, KRON_CHEB_FILT>(a, s);
+                case KRON_CORI: return kron_chunk_launch<T, 3, KRON_CORI>(a, s);
+            }
+        } else if (R == 1 && mode == KRON_CHEB) {
+            return kron_chunk_launch<T, 1, KRON_CHEB>(a, s);
         }
     }
     if constexpr (std::is_same<T, float>::value) {

@@ -49,6 +49,13 @@ struct KronArgs {
     // zeroed by the launcher on the stream before the launch
     int* sched = nullptr;
     int nreg = 0;
+    // chunked warp-per-row schedule (b = 17..64): threads per CTA
+    // (256, 512 or 1024), 0 = off
+    int chunk = 0;
+    // float blocks 32 wide with ldx = 32: 1 = 16-byte vectorised gathers
+    // (four groups of eight lanes per row), 0 = scalar gathers
+    int vec = 1;
+    int vec_threads = 256;   // CTA size of the vectorised kernel (256, 512, 1024)
 };
 
 template <typename T>

@@ -136,6 +136,9 @@ struct nm_problem {
     int use_df = 1;
     // SM-local persistent schedule of the semi-iteration kernels
     int use_sched = 0;
+    int use_vec = 1;      // vectorised gathers for float b = 32 blocks
+    int vec_threads = 256;  // their CTA size
+    int use_chunk = 0;    // threads per CTA of the chunked row schedule, 0 = off
     nm::DevBuf sched;   // int [nreg] region counters
     int nreg = 0;
     // scratch for the filter recurrence

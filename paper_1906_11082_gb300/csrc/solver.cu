@@ -87,6 +87,9 @@ static Mats<T> mats(nm_problem* P) {
 
 template <typename T>
 static void set_sched(KronArgs<T>& a, nm_problem* P) {
+    a.chunk = P->use_chunk;
+    a.vec = P->use_vec;
+    a.vec_threads = P->vec_threads;
     if (P->use_sched && P->sched.p) {
         a.sched = P->sched.as<int>();
         a.nreg = P->nreg;
@@ -825,14 +828,18 @@ int autotune(nm_problem* P, int b, nm_prec prec, int k_M, std::string* report) {
     } else {
         NM_TRY(launch_philox_normal(n * 64, 7, Y.as<double>(), s));
     }
-    struct Cfg { int sched, tile, tk, df; };
+    struct Cfg { int sched, tile, tk, df, chunk, vec; };
     std::vector<Cfg> cfgs;
+    const int df1 = prec == NM_MIXED ? 1 : P->use_df;
     for (int sched : {0, 1})
         for (int df : (prec == NM_MIXED ? std::vector<int>{1, 0} : std::vector<int>{P->use_df}))
-            cfgs.push_back({sched, 0, 2, df});
+            cfgs.push_back({sched, 0, 2, df, 0, 1});
+    if (prec != NM_F64 && b == 32) cfgs.push_back({0, 0, 2, df1, 0, 0});
+    if (b >= 17)
+        for (int ch : {256, 512, 1024}) cfgs.push_back({0, 0, 2, df1, ch, 0});
     if (prec != NM_F64 && b == 32) {
-        cfgs.push_back({0, 16, 2, prec == NM_MIXED ? 1 : P->use_df});
-        cfgs.push_back({0, 32, 2, prec == NM_MIXED ? 1 : P->use_df});
+        cfgs.push_back({0, 16, 2, df1, 0, 0});
+        cfgs.push_back({0, 32, 2, df1, 0, 0});
     }
     const int reps = 2;
     double best = 1e300;
@@ -842,14 +849,18 @@ int autotune(nm_problem* P, int b, nm_prec prec, int k_M, std::string* report) {
         const Cfg& c = cfgs[i];
         P->use_sched = c.sched;
         P->use_df = c.df;
+        P->use_chunk = c.chunk;
+        P->use_vec = c.vec;
         NM_TRY(set_tile_rows(P, c.tile));
         if (c.tile) P->Mr.tile_kernel = P->Pn.tile_kernel = c.tk;
         double ms = 0;
         NM_TRY(time_degree(P, b, prec, k_M, Y.p, Z.p, reps, &ms));
         ms /= reps;
         char buf[160];
-        snprintf(buf, sizeof buf, "%s{\"sched\": %d, \"tile_rows\": %d, \"double_float\": %d, \"ms_per_degree\": %.4f}",
-                 i ? ", " : "", c.sched, c.tile, c.df, ms);
+        snprintf(buf, sizeof buf,
+                 "%s{\"sched\": %d, \"chunk\": %d, \"vec\": %d, \"tile_rows\": %d, \"double_float\": %d, "
+                 "\"ms_per_degree\": %.4f}",
+                 i ? ", " : "", c.sched, c.chunk, c.vec, c.tile, c.df, ms);
         rep += buf;
         if (ms < best) {
             best = ms;
@@ -858,9 +869,12 @@ int autotune(nm_problem* P, int b, nm_prec prec, int k_M, std::string* report) {
     }
     P->use_sched = bestc.sched;
     P->use_df = bestc.df;
+    P->use_chunk = bestc.chunk;
+    P->use_vec = bestc.vec;
     NM_TRY(set_tile_rows(P, bestc.tile));
     if (bestc.tile) P->Mr.tile_kernel = P->Pn.tile_kernel = bestc.tk;
-    rep += "], \"chosen\": {\"sched\": " + std::to_string(bestc.sched) + ", \"tile_rows\": " +
+    rep += "], \"chosen\": {\"sched\": " + std::to_string(bestc.sched) + ", \"chunk\": " +
+           std::to_string(bestc.chunk) + ", \"vec\": " + std::to_string(bestc.vec) + ", \"tile_rows\": " +
            std::to_string(bestc.tile) + ", \"double_float\": " + std::to_string(bestc.df) + "}, \"us_per_column_degree\": {";
     int first = 1;
     for (int bb : {16, 32, 64}) {

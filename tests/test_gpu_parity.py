@@ -389,7 +389,7 @@ def test_tile_options_agree(nm, planet):
             P.solve_M(W, X, 15)
             outs.append(_host(X))
     finally:
-        P.set_option("tile_rows", 16)
+        P.set_option("tile_rows", 0)
         P.set_option("tile_kernel", 2)
     for o in outs[1:]:
         assert rel_err(o, outs[0]) <= 1e-5
@@ -397,6 +397,83 @@ def test_tile_options_agree(nm, planet):
         P.set_option("tile_rows", 3)
     with pytest.raises(nm.NMError):
         P.set_option("no_such_option", 1)
+
+
+@pytest.mark.parametrize("chunk", [256, 512, 1024])
+def test_chunk_options_agree(nm, planet, chunk):
+    """The chunked row schedule runs the same per-row code as the plain
+    warp-per-row grid, so mass solves (float b = 32, double b = 40), the
+    float pressure solve inside K_eff and a mixed filter agree with it to
+    the last bits (bounded here by 1e-6 / 1e-14 relative)."""
+    mesh, model, S, P = planet
+    rng = np.random.default_rng(17)
+    W32 = _dev(rng.standard_normal((S.n, 32)), torch.float32)
+    W64 = _dev(rng.standard_normal((S.n, 40)))
+    K64 = _dev(rng.standard_normal((S.n, 24)))
+    lo, hi = P.spectrum_bounds(k_M=20)
+    gam, c, e = nm.filter_design(lo, hi, 0.5, 9.0, 6)
+
+    def run():
+        X32, X64, Y32, Z = (torch.empty_like(W32), torch.empty_like(W64),
+                            torch.empty_like(W32), torch.empty_like(K64))
+        P.solve_M(W32, X32, 15)
+        P.solve_M(W64, X64, 15)
+        P.apply_K(W32, Y32, k_P=12)
+        P.filter_apply(gam, c, e, 20, K64, Z, prec=nm.NM_MIXED)
+        return [_host(v) for v in (X32, X64, Y32, Z)]
+
+    try:
+        P.set_option("vec", 0)          # the chunked schedule runs the scalar-gather row code
+        base = run()
+        P.set_option("chunk", chunk)
+        got = run()
+    finally:
+        P.set_option("chunk", 0)
+        P.set_option("vec", 1)
+    for o, r, tol in zip(got, base, (1e-6, 1e-14, 1e-6, 1e-14)):
+        assert rel_err(o, r) <= tol
+    with pytest.raises(nm.NMError):
+        P.set_option("chunk", 300)
+
+
+def test_vec_option_agrees(nm, planet):
+    """The 16-byte vectorised gathers (float, b = 32) sum each row in a
+    different order than the scalar ones: float mass solve, float pressure
+    solve inside K_eff and a whole FP32 filter agree with them to float
+    rounding (1e-5 relative), and with the oracle as the FP32 tests state."""
+    mesh, model, S, P = planet
+    rng = np.random.default_rng(19)
+    Wc = rng.standard_normal((S.n, 32))
+    W32 = _dev(to_internal(P, Wc), torch.float32)
+    op = filtlan.Operator(S, k_M=15, k_P=15)
+    lo, hi = filtlan.spectrum_bounds(op, S.n)
+    gam, c, e = filtlan.filter_coeffs(lo, hi, 0.5, 9.0, 8)
+
+    def run():
+        X, Y, Z = torch.empty_like(W32), torch.empty_like(W32), torch.empty_like(W32)
+        P.solve_M(W32, X, 15)
+        P.apply_K(W32, Y, k_P=15)
+        P.filter_apply(gam, c, e, 15, W32, Z, k_P=15)
+        return [_host(v) for v in (X, Y, Z)]
+
+    vec = run()
+    try:
+        P.set_option("sched", 1)        # SM-local row order: same per-row code
+        sched = run()
+        P.set_option("sched", 0)
+        P.set_option("vec", 0)
+        scal = run()
+    finally:
+        P.set_option("vec", 1)
+        P.set_option("sched", 0)
+    for o, r in zip(sched, vec):
+        assert rel_err(o, r) <= 1e-6
+    for o, r in zip(vec, scal):
+        assert rel_err(o, r) <= 1e-5
+    assert rel_err(to_canonical(P, vec[1]), op.K(Wc)) <= 1e-4
+    assert rel_err(to_canonical(P, vec[2]), filtlan.filter_apply(op, gam, c, e, Wc)) <= 1e-3
+    with pytest.raises(nm.NMError):
+        P.set_option("vec", 2)
 
 
 def test_autotune_report_and_results(nm, planet):
