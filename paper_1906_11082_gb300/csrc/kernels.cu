@@ -1224,6 +1224,155 @@ __global__ void __launch_bounds__(kThreads) resid_df_kernel(int64_t nodes, const
     }
 }
 
+// Dot2-style double-float accumulation (Ogita, Rump and Oishi): the
+// rounding error of each product (exact via FMA), the first-order terms of
+// the operands' low parts and the TwoSum error of each addition are
+// collected in sl; sh carries the running float sum. sl stays ~n ulp(sh),
+// so it needs no renormalisation until the final (double) sh + sl.
+__device__ __forceinline__ void df_acc(float& sh, float& sl, float ah, float al, float xh, float xl) {
+    const float p = __fmul_rn(ah, xh);
+    const float e = __fmaf_rn(ah, xh, -p);
+    const float t = __fmaf_rn(ah, xl, __fmaf_rn(al, xh, e));
+    const float s = __fadd_rn(sh, p);
+    const float bp = __fadd_rn(s, -sh);
+    const float err = __fadd_rn(__fadd_rn(sh, -__fadd_rn(s, -bp)), __fadd_rn(p, -bp));
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(err, t));
+}
+
+// (sh, sl) += (h2, l2) for two Dot2 accumulators.
+__device__ __forceinline__ void df_merge(float& sh, float& sl, float h2, float l2) {
+    const float s = __fadd_rn(sh, h2);
+    const float bp = __fadd_rn(s, -sh);
+    const float err = __fadd_rn(__fadd_rn(sh, -__fadd_rn(s, -bp)), __fadd_rn(h2, -bp));
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(err, l2));
+}
+
+// Butterfly-combine the four lane groups' accumulators (lanes q, q + 8,
+// q + 16, q + 24 hold partial sums of the same four columns).
+template <int N>
+__device__ __forceinline__ void df_group_reduce(float (&sh)[N], float (&sl)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int m = 8; m <= 16; m *= 2) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, sh[i], m);
+            const float l2 = __shfl_xor_sync(0xffffffffu, sl[i], m);
+            df_merge(sh[i], sl[i], h2, l2);
+        }
+    }
+}
+
+// W = A X (+ E S) in double-float for blocks exactly 32 wide with the split
+// operand stored densely (ld 32): one warp per 3x3-block row, four groups
+// of eight lanes taking every fourth stored block, lane q of a group
+// holding columns 4q..4q+3 of the three output components and reading the
+// neighbour's (hi, lo) records with 16-byte loads. After the groups are
+// combined, group m < 3 writes output component m (and adds the pressure
+// coupling in double, as the generic kernel does).
+__global__ void __launch_bounds__(kThreads, 4) bsr33_df_v4_kernel(const Bsr33DfArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 3, q = lane & 7;
+    const int64_t row = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (row >= a.nrows) return;
+    float sh[12], sl[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) sh[i] = sl[i] = 0.f;
+    const int e0 = __ldg(a.rowptr + row), e1 = __ldg(a.rowptr + row + 1);
+    const float4* xh4 = reinterpret_cast<const float4*>(a.Xh) + q;
+    const float4* xl4 = reinterpret_cast<const float4*>(a.Xl) + q;
+    for (int e = e0 + g; e < e1; e += 4) {
+        const int64_t j = __ldg(a.col + e);
+        const float* kh = a.vh + 9 * (int64_t)e;
+        const float* kl = a.vl + 9 * (int64_t)e;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 xh = __ldg(xh4 + j * 24 + 8 * k);
+            const float4 xl = __ldg(xl4 + j * 24 + 8 * k);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const float ah = __ldg(kh + 3 * m + k), al = __ldg(kl + 3 * m + k);
+                df_acc(sh[4 * m + 0], sl[4 * m + 0], ah, al, xh.x, xl.x);
+                df_acc(sh[4 * m + 1], sl[4 * m + 1], ah, al, xh.y, xl.y);
+                df_acc(sh[4 * m + 2], sl[4 * m + 2], ah, al, xh.z, xl.z);
+                df_acc(sh[4 * m + 3], sl[4 * m + 3], ah, al, xh.w, xl.w);
+            }
+        }
+    }
+    df_group_reduce<12>(sh, sl);
+    if (g >= 3) return;
+    const int m = g;
+    double acc[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float h = m == 0 ? sh[c] : (m == 1 ? sh[4 + c] : sh[8 + c]);
+        const float l = m == 0 ? sl[c] : (m == 1 ? sl[4 + c] : sl[8 + c]);
+        acc[c] = (double)h + (double)l;
+    }
+    if (a.e_rowptr) {
+        const int f0 = __ldg(a.e_rowptr + row), f1 = __ldg(a.e_rowptr + row + 1);
+        for (int f = f0; f < f1; ++f) {
+            const int64_t p = __ldg(a.e_col + f);
+            const double ev = __ldg(a.e_val + 3 * (int64_t)f + m);
+            const double* sp = a.S + p * a.lds + 4 * q;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c] += ev * __ldg(sp + c);
+        }
+    }
+    double* wp = a.W + (3 * row + m) * a.ldw + 4 * q;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) wp[c] = acc[c];
+}
+
+// r32 = float(W - (A (x) I_R) x32) for blocks exactly 32 wide (x32 and r32
+// dense, ld 32), with the lane-group layout of bsr33_df_v4_kernel.
+template <int R>
+__global__ void __launch_bounds__(kThreads, 4) resid_df_v4_kernel(int64_t nodes, const int* __restrict__ rowptr,
+                                                                  const int* __restrict__ col,
+                                                                  const float* __restrict__ vh,
+                                                                  const float* __restrict__ vl,
+                                                                  const double* __restrict__ W, int64_t ldw,
+                                                                  const float* __restrict__ x, float* r) {
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 3, q = lane & 7;
+    const int64_t row = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (row >= nodes) return;
+    float sh[4 * R], sl[4 * R];
+#pragma unroll
+    for (int i = 0; i < 4 * R; ++i) sh[i] = sl[i] = 0.f;
+    const int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
+    const float4* x4 = reinterpret_cast<const float4*>(x) + q;
+    for (int e = e0 + g; e < e1; e += 4) {
+        const int64_t j = __ldg(col + e);
+        const float mh = __ldg(vh + e), ml = __ldg(vl + e);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const float4 xv = __ldg(x4 + j * (8 * R) + 8 * k);
+            df_acc(sh[4 * k + 0], sl[4 * k + 0], mh, ml, xv.x, 0.f);
+            df_acc(sh[4 * k + 1], sl[4 * k + 1], mh, ml, xv.y, 0.f);
+            df_acc(sh[4 * k + 2], sl[4 * k + 2], mh, ml, xv.z, 0.f);
+            df_acc(sh[4 * k + 3], sl[4 * k + 3], mh, ml, xv.w, 0.f);
+        }
+    }
+    df_group_reduce<4 * R>(sh, sl);
+    if (g >= R) return;
+    const int k = g;
+    const int64_t rr = R * row + k;
+    const double* wp = W + rr * ldw + 4 * q;
+    float out[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float h = sh[c], l = sl[c];
+        if (R == 3) {
+            h = k == 0 ? sh[c] : (k == 1 ? sh[4 + c] : sh[8 + c]);
+            l = k == 0 ? sl[c] : (k == 1 ? sl[4 + c] : sl[8 + c]);
+        }
+        out[c] = (float)((wp[c] - (double)h) - (double)l);
+    }
+    reinterpret_cast<float4*>(r + rr * 32)[q] = make_float4(out[0], out[1], out[2], out[3]);
+}
+
 int launch_split(int64_t rows, int b, const double* X, int64_t ldx, float* Xh, float* Xl, cudaStream_t s) {
     if (rows * b == 0) return NM_OK;
     split_kernel<<<grid_for(rows * b), kThreads, 0, s>>>(rows, b, X, ldx, Xh, Xl);
@@ -1234,6 +1383,14 @@ int launch_split(int64_t rows, int b, const double* X, int64_t ldx, float* Xh, f
 
 int launch_bsr33_df(const Bsr33DfArgs& a, cudaStream_t s) {
     if (a.b < 1 || a.b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
+    if (a.vec && a.b == 32 && (((uintptr_t)a.Xh | (uintptr_t)a.Xl) & 15) == 0) {
+        const int64_t grid = (a.nrows + kThreads / 32 - 1) / (kThreads / 32);
+        if (grid == 0) return NM_OK;
+        bsr33_df_v4_kernel<<<(unsigned)grid, kThreads, 0, s>>>(a);
+        count_launch();
+        NM_CUDA(cudaGetLastError());
+        return NM_OK;
+    }
     const int shift = tpr_shift_for(a.b);
     const int cpt = (a.b + (1 << shift) - 1) >> shift;
     const int64_t grid = (a.nrows + (kThreads >> shift) - 1) / (kThreads >> shift);
@@ -1248,8 +1405,19 @@ int launch_bsr33_df(const Bsr33DfArgs& a, cudaStream_t s) {
 }
 
 int launch_resid_df(int R, int64_t nodes, const int* rowptr, const int* col, const float* vh, const float* vl,
-                    const double* W, int64_t ldw, const float* x32, float* r32, int b, cudaStream_t s) {
+                    const double* W, int64_t ldw, const float* x32, float* r32, int b, cudaStream_t s, int vec) {
     if (b < 1 || b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
+    if (vec && b == 32 && (((uintptr_t)x32 | (uintptr_t)r32) & 15) == 0) {
+        const int64_t grid = (nodes + kThreads / 32 - 1) / (kThreads / 32);
+        if (grid == 0) return NM_OK;
+        if (R == 3)
+            resid_df_v4_kernel<3><<<(unsigned)grid, kThreads, 0, s>>>(nodes, rowptr, col, vh, vl, W, ldw, x32, r32);
+        else
+            resid_df_v4_kernel<1><<<(unsigned)grid, kThreads, 0, s>>>(nodes, rowptr, col, vh, vl, W, ldw, x32, r32);
+        count_launch();
+        NM_CUDA(cudaGetLastError());
+        return NM_OK;
+    }
     const int shift = tpr_shift_for(b);
     const int cpt = (b + (1 << shift) - 1) >> shift;
     const int64_t grid = (nodes + (kThreads >> shift) - 1) / (kThreads >> shift);

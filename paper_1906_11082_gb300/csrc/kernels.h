@@ -156,11 +156,14 @@ struct Bsr33DfArgs {
     int64_t lds = 0;
     double* W = nullptr;
     int64_t ldw = 0;
+    int vec = 1;   // b = 32 with 16-byte aligned operands: lane-group kernel
 };
 int launch_bsr33_df(const Bsr33DfArgs& a, cudaStream_t s);
-// r32 = float(W - (A (x) I_R) x32) with A as (hi, lo) floats, double-float sums.
+// r32 = float(W - (A (x) I_R) x32) with A as (hi, lo) floats, double-float
+// sums; x32 and r32 dense (ld b). vec: lane-group kernel when b = 32.
 int launch_resid_df(int R, int64_t nodes, const int* rowptr, const int* col, const float* vh, const float* vl,
-                    const double* W, int64_t ldw, const float* x32, float* r32, int b, cudaStream_t s);
+                    const double* W, int64_t ldw, const float* x32, float* r32, int b, cudaStream_t s,
+                    int vec = 1);
 
 // Y[i, c] = alpha * X[i, c] (rows x b, row-major with leading dims).
 template <typename T>

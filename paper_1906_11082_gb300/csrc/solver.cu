@@ -431,7 +431,7 @@ static int mixed_solve(nm_problem* P, const DevCSR& A, int R, int b, int k, cons
     NM_TRY(cheb32(P, A, R, b, k, kMassLo, kMassHi, S.w32, S.xa, S.xb, S.xs, s));
     if (df)
         NM_TRY(launch_resid_df(R, A.nrows, A.rowptr.as<int>(), A.col.as<int>(), A.val32.as<float>(),
-                               A.vlo32.as<float>(), W, ldw, S.xs, S.w32, b, s));
+                               A.vlo32.as<float>(), W, ldw, S.xs, S.w32, b, s, P->use_vec));
     else
         NM_TRY(launch_resid_mixed(R, A.nrows, A.rowptr.as<int>(), A.col.as<int>(), A.val.as<double>(), W, ldw,
                                   S.xs, S.w32, b, s));
@@ -497,6 +497,7 @@ static int apply_K_mixed(nm_problem* P, const double* X, int64_t ldx, double* W,
     f.lds = a.lds;
     f.W = W;
     f.ldw = ldw;
+    f.vec = P->use_vec;
     return launch_bsr33_df(f, s);
 }
 

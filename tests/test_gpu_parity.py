@@ -350,13 +350,15 @@ def test_invalid_block_width(nm, ball):
     assert e.value.code == nm.NM_EINVAL
 
 
-def test_double_float_matches_double(nm, planet):
+@pytest.mark.parametrize("b", [8, 32])
+def test_double_float_matches_double(nm, planet, b):
     """The mixed form's double-float SpMMs agree with the double ones to
     about 2^-48 per term; the float semi-iterations downstream then carry
     their own rounding (~6e-8 x the 1e-4-size refinement residual), so the
-    outputs agree to ~1e-11 relative to the largest entry."""
+    outputs agree to ~1e-11 relative to the largest entry. b = 32 runs the
+    lane-group (16-byte load) double-float kernels, b = 8 the generic ones."""
     mesh, model, S, P = planet
-    Xc = np.random.default_rng(12).standard_normal((S.n, 8))
+    Xc = np.random.default_rng(12).standard_normal((S.n, b))
     X = _dev(to_internal(P, Xc))
     Y0, Y1 = torch.empty_like(X), torch.empty_like(X)
     try:
