@@ -188,9 +188,13 @@ int nm_problem_export(const nm_problem* prob, int which, int64_t* nrows, int64_t
  * precedence over the other schedules. key "vec": 1 (default) runs the float semi-iteration SpMMs
  * of blocks exactly 32 wide with ld = 32 with 16-byte vectorised gathers
  * (each row split over four groups of eight lanes), 0 with one 4-byte
- * gather per lane and component; key "vec_threads" (256 default, 512,
- * 1024) sets their CTA size, i.e. how many consecutive rows share an SM's
- * L1. key "tile_rows": height of the row
+ * gather per lane and component; key "vec_threads" (32 default, 64, 128,
+ * 256, 512, 1024; one row per warp) sets their CTA size for the
+ * 3-component mass rows, "vec_threads_p" (128 default) for the
+ * 1-component pressure rows: larger CTAs put more consecutive rows on one
+ * SM's L1, smaller ones free their slot sooner when a CTA's rows differ in
+ * length. key "df_threads" (32 default, 64, 128, 256): CTA size of the
+ * NM_MIXED form's lane-group double-float SpMMs (b = 32). key "tile_rows": height of the row
  * tiles whose gathered operand the float kernels stage in shared memory
  * (0, the default, disables staging; 4..64, power of two); the tiles are
  * rebuilt on the host. key "tile_kernel": 1 or 2, the staged kernel
@@ -314,9 +318,12 @@ int nm_ritz(nm_problem* prob, nm_ritz_mode mode, const double* V, int64_t ldv, i
 /* ---- kernel timing --------------------------------------------------------
  * With profiling enabled, every filter degree brackets its launch
  * sequences with CUDA events on the launching stream: kind 0 = the mass
- * solve's semi-iteration steps (k_M - 1 back-to-back launches of the
- * fused M_rho SpMM + update kernel), kind 1 = the K_eff application
- * (E_G^T SpMM, the pressure semi-iteration, the A_G (+ E_G) SpMM).
+ * solve (NM_F64 / NM_F32: its k_M - 1 back-to-back launches of the fused
+ * M_rho SpMM + update kernel; NM_MIXED: the whole refined solve, 2 k_M + 3
+ * launches), kind 1 = the K_eff application (E_G^T SpMM, the pressure
+ * semi-iteration, the A_G (+ E_G) SpMM), kind 2 = NM_MIXED only: the
+ * float M_rho semi-iteration launches alone (k_M - 1 back-to-back launches
+ * per half of each refined mass solve).
  * nm_profile_read synchronises the problem's recorded streams and returns
  * the launch count and summed device milliseconds of a kind since the
  * last reset. Profiling adds two events per region and degree. */

@@ -223,9 +223,16 @@ int nm_set_option(nm_problem* P, const char* key, int64_t value) {
         P->use_vec = (int)value;
         return NM_OK;
     }
-    if (std::string(key) == "vec_threads") {
-        if (value != 256 && value != 512 && value != 1024) return fail(NM_EINVAL, "vec_threads must be 256, 512 or 1024");
-        P->vec_threads = (int)value;
+    if (std::string(key) == "vec_threads" || std::string(key) == "vec_threads_p") {
+        if (value != 32 && value != 64 && value != 128 && value != 256 && value != 512 && value != 1024)
+            return fail(NM_EINVAL, std::string(key) + " must be 32, 64, 128, 256, 512 or 1024");
+        (std::string(key) == "vec_threads" ? P->vec_threads : P->vec_threads_p) = (int)value;
+        return NM_OK;
+    }
+    if (std::string(key) == "df_threads") {
+        if (value != 32 && value != 64 && value != 128 && value != 256)
+            return fail(NM_EINVAL, "df_threads must be 32, 64, 128 or 256");
+        P->df_threads = (int)value;
         return NM_OK;
     }
     if (std::string(key) == "chunk") {
@@ -419,7 +426,7 @@ uint64_t nm_kernel_launches(void) { return launches_so_far(); }
 
 int nm_profile_read(nm_problem* P, int kind, int64_t* launches, double* ms) {
     if (!P || !launches || !ms) return fail(NM_EINVAL, "null argument");
-    if (kind < 0 || kind > 1) return fail(NM_EINVAL, "kind must be 0 or 1");
+    if (kind < 0 || kind > 2) return fail(NM_EINVAL, "kind must be 0, 1 or 2");
     CtxScope sc(P->ctx);
     return profile_read(P, kind, launches, ms);
 }

@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(1024) kron_chunk_kernel(const KronArgs<T> a) {
 // combined by butterfly shuffles and lane c then takes column c for the
 // shared epilogue.
 template <int R, int MODE, int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) kron_v4_kernel(const KronArgs<float> a) {
+__global__ void __launch_bounds__(NT, 1024 / NT) kron_v4_kernel(const KronArgs<float> a) {
     const int lane = threadIdx.x & 31;
     const int g = lane >> 3, q = lane & 7;
     int64_t blk = blockIdx.x;
@@ -504,34 +504,34 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) kron_
         }
     }
     const float4* xb = reinterpret_cast<const float4*>(a.X) + q;
+    // entries per group in flight: a 1-component record is a quarter of a
+    // 3-component one, so it takes twice as many to keep the loads busy
+    constexpr int U = R == 1 ? 4 : 2;
     int e = e0 + g;
-    for (; e + 4 < e1; e += 8) {
-        const int j0 = __ldg(a.col + e), j1 = __ldg(a.col + e + 4);
-        const float v0 = __ldg(a.val + e), v1 = __ldg(a.val + e + 4);
-        const float4* p0 = xb + (int64_t)j0 * (8 * R);
-        const float4* p1 = xb + (int64_t)j1 * (8 * R);
-        float4 x0[R], x1[R];
+    for (; e + 4 * (U - 1) < e1; e += 4 * U) {
+        int j[U];
+        float v[U];
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
-            x0[k] = __ldg(p0 + 8 * k);
-            x1[k] = __ldg(p1 + 8 * k);
+        for (int u = 0; u < U; ++u) {
+            j[u] = __ldg(a.col + e + 4 * u);
+            v[u] = __ldg(a.val + e + 4 * u);
         }
+        float4 x[U][R];
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
-            acc[k].x += v0 * x0[k].x;
-            acc[k].y += v0 * x0[k].y;
-            acc[k].z += v0 * x0[k].z;
-            acc[k].w += v0 * x0[k].w;
-        }
+        for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
-            acc[k].x += v1 * x1[k].x;
-            acc[k].y += v1 * x1[k].y;
-            acc[k].z += v1 * x1[k].z;
-            acc[k].w += v1 * x1[k].w;
-        }
+            for (int k = 0; k < R; ++k) x[u][k] = __ldg(xb + (int64_t)j[u] * (8 * R) + 8 * k);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                acc[k].x += v[u] * x[u][k].x;
+                acc[k].y += v[u] * x[u][k].y;
+                acc[k].z += v[u] * x[u][k].z;
+                acc[k].w += v[u] * x[u][k].w;
+            }
     }
-    if (e < e1) {
+    for (; e < e1; e += 4) {
         const int j0 = __ldg(a.col + e);
         const float v0 = __ldg(a.val + e);
         const float4* p0 = xb + (int64_t)j0 * (8 * R);
@@ -590,16 +590,18 @@ template <int R, int MODE>
 static int kron_v4_launch(const KronArgs<float>& a, cudaStream_t s) {
     // one row per warp; larger CTAs keep more consecutive (Morton-near)
     // rows, whose neighbour sets overlap, on one SM's L1
-    const int nt = a.vec_threads == 512 || a.vec_threads == 1024 ? a.vec_threads : 256;
+    const int nt = R == 1 ? a.vec_threads_p : a.vec_threads;
     const int64_t grid = (a.nrows + nt / 32 - 1) / (nt / 32);
     if (grid == 0) return NM_OK;
     if (a.sched) NM_CUDA(cudaMemsetAsync(a.sched, 0, a.nreg * sizeof(int), s));
-    if (nt == 1024)
-        kron_v4_kernel<R, MODE, 1024><<<(unsigned)grid, 1024, 0, s>>>(a);
-    else if (nt == 512)
-        kron_v4_kernel<R, MODE, 512><<<(unsigned)grid, 512, 0, s>>>(a);
-    else
-        kron_v4_kernel<R, MODE, 256><<<(unsigned)grid, 256, 0, s>>>(a);
+    switch (nt) {
+        case 32: kron_v4_kernel<R, MODE, 32><<<(unsigned)grid, 32, 0, s>>>(a); break;
+        case 64: kron_v4_kernel<R, MODE, 64><<<(unsigned)grid, 64, 0, s>>>(a); break;
+        case 128: kron_v4_kernel<R, MODE, 128><<<(unsigned)grid, 128, 0, s>>>(a); break;
+        case 512: kron_v4_kernel<R, MODE, 512><<<(unsigned)grid, 512, 0, s>>>(a); break;
+        case 1024: kron_v4_kernel<R, MODE, 1024><<<(unsigned)grid, 1024, 0, s>>>(a); break;
+        default: kron_v4_kernel<R, MODE, 256><<<(unsigned)grid, 256, 0, s>>>(a); break;
+    }
     count_launch();
     NM_CUDA(cudaGetLastError());
     return NM_OK;
@@ -1271,10 +1273,11 @@ __device__ __forceinline__ void df_group_reduce(float (&sh)[N], float (&sl)[N]) 
 // neighbour's (hi, lo) records with 16-byte loads. After the groups are
 // combined, group m < 3 writes output component m (and adds the pressure
 // coupling in double, as the generic kernel does).
-__global__ void __launch_bounds__(kThreads, 4) bsr33_df_v4_kernel(const Bsr33DfArgs a) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) bsr33_df_v4_kernel(const Bsr33DfArgs a) {
     const int lane = threadIdx.x & 31;
     const int g = lane >> 3, q = lane & 7;
-    const int64_t row = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const int64_t row = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
     if (row >= a.nrows) return;
     float sh[12], sl[12];
 #pragma unroll
@@ -1327,8 +1330,8 @@ __global__ void __launch_bounds__(kThreads, 4) bsr33_df_v4_kernel(const Bsr33DfA
 
 // r32 = float(W - (A (x) I_R) x32) for blocks exactly 32 wide (x32 and r32
 // dense, ld 32), with the lane-group layout of bsr33_df_v4_kernel.
-template <int R>
-__global__ void __launch_bounds__(kThreads, 4) resid_df_v4_kernel(int64_t nodes, const int* __restrict__ rowptr,
+template <int R, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) resid_df_v4_kernel(int64_t nodes, const int* __restrict__ rowptr,
                                                                   const int* __restrict__ col,
                                                                   const float* __restrict__ vh,
                                                                   const float* __restrict__ vl,
@@ -1336,7 +1339,7 @@ __global__ void __launch_bounds__(kThreads, 4) resid_df_v4_kernel(int64_t nodes,
                                                                   const float* __restrict__ x, float* r) {
     const int lane = threadIdx.x & 31;
     const int g = lane >> 3, q = lane & 7;
-    const int64_t row = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const int64_t row = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
     if (row >= nodes) return;
     float sh[4 * R], sl[4 * R];
 #pragma unroll
@@ -1384,9 +1387,15 @@ int launch_split(int64_t rows, int b, const double* X, int64_t ldx, float* Xh, f
 int launch_bsr33_df(const Bsr33DfArgs& a, cudaStream_t s) {
     if (a.b < 1 || a.b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
     if (a.vec && a.b == 32 && (((uintptr_t)a.Xh | (uintptr_t)a.Xl) & 15) == 0) {
-        const int64_t grid = (a.nrows + kThreads / 32 - 1) / (kThreads / 32);
+        const int nt = a.nt;
+        const int64_t grid = (a.nrows + nt / 32 - 1) / (nt / 32);
         if (grid == 0) return NM_OK;
-        bsr33_df_v4_kernel<<<(unsigned)grid, kThreads, 0, s>>>(a);
+        switch (nt) {
+            case 32: bsr33_df_v4_kernel<32><<<(unsigned)grid, 32, 0, s>>>(a); break;
+            case 64: bsr33_df_v4_kernel<64><<<(unsigned)grid, 64, 0, s>>>(a); break;
+            case 128: bsr33_df_v4_kernel<128><<<(unsigned)grid, 128, 0, s>>>(a); break;
+            default: bsr33_df_v4_kernel<256><<<(unsigned)grid, 256, 0, s>>>(a); break;
+        }
         count_launch();
         NM_CUDA(cudaGetLastError());
         return NM_OK;
@@ -1405,15 +1414,30 @@ int launch_bsr33_df(const Bsr33DfArgs& a, cudaStream_t s) {
 }
 
 int launch_resid_df(int R, int64_t nodes, const int* rowptr, const int* col, const float* vh, const float* vl,
-                    const double* W, int64_t ldw, const float* x32, float* r32, int b, cudaStream_t s, int vec) {
+                    const double* W, int64_t ldw, const float* x32, float* r32, int b, cudaStream_t s, int vec,
+                    int nt) {
     if (b < 1 || b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
     if (vec && b == 32 && (((uintptr_t)x32 | (uintptr_t)r32) & 15) == 0) {
-        const int64_t grid = (nodes + kThreads / 32 - 1) / (kThreads / 32);
+        if (nt != 32 && nt != 64 && nt != 128) nt = 256;
+        const int64_t grid = (nodes + nt / 32 - 1) / (nt / 32);
         if (grid == 0) return NM_OK;
-        if (R == 3)
-            resid_df_v4_kernel<3><<<(unsigned)grid, kThreads, 0, s>>>(nodes, rowptr, col, vh, vl, W, ldw, x32, r32);
-        else
-            resid_df_v4_kernel<1><<<(unsigned)grid, kThreads, 0, s>>>(nodes, rowptr, col, vh, vl, W, ldw, x32, r32);
+#define NM_RESID_V4(RR, NN) resid_df_v4_kernel<RR, NN><<<(unsigned)grid, NN, 0, s>>>(nodes, rowptr, col, vh, vl, W, ldw, x32, r32)
+        if (R == 3) {
+            switch (nt) {
+                case 32: NM_RESID_V4(3, 32); break;
+                case 64: NM_RESID_V4(3, 64); break;
+                case 128: NM_RESID_V4(3, 128); break;
+                default: NM_RESID_V4(3, 256); break;
+            }
+        } else {
+            switch (nt) {
+                case 32: NM_RESID_V4(1, 32); break;
+                case 64: NM_RESID_V4(1, 64); break;
+                case 128: NM_RESID_V4(1, 128); break;
+                default: NM_RESID_V4(1, 256); break;
+            }
+        }
+#undef NM_RESID_V4
         count_launch();
         NM_CUDA(cudaGetLastError());
         return NM_OK;

@@ -55,7 +55,8 @@ struct KronArgs {
     // float blocks 32 wide with ldx = 32: 1 = 16-byte vectorised gathers
     // (four groups of eight lanes per row), 0 = scalar gathers
     int vec = 1;
-    int vec_threads = 256;   // CTA size of the vectorised kernel (256, 512, 1024)
+    int vec_threads = 32;    // CTA size of the vectorised kernel, R = 3 (32 .. 1024, power of two)
+    int vec_threads_p = 128; // the same for R = 1
 };
 
 template <typename T>
@@ -157,13 +158,14 @@ struct Bsr33DfArgs {
     double* W = nullptr;
     int64_t ldw = 0;
     int vec = 1;   // b = 32 with 16-byte aligned operands: lane-group kernel
+    int nt = 256;  // its CTA size (32, 64, 128, 256)
 };
 int launch_bsr33_df(const Bsr33DfArgs& a, cudaStream_t s);
 // r32 = float(W - (A (x) I_R) x32) with A as (hi, lo) floats, double-float
 // sums; x32 and r32 dense (ld b). vec: lane-group kernel when b = 32.
 int launch_resid_df(int R, int64_t nodes, const int* rowptr, const int* col, const float* vh, const float* vl,
                     const double* W, int64_t ldw, const float* x32, float* r32, int b, cudaStream_t s,
-                    int vec = 1);
+                    int vec = 1, int nt = 256);
 
 // Y[i, c] = alpha * X[i, c] (rows x b, row-major with leading dims).
 template <typename T>

@@ -137,7 +137,9 @@ struct nm_problem {
     // SM-local persistent schedule of the semi-iteration kernels
     int use_sched = 0;
     int use_vec = 1;      // vectorised gathers for float b = 32 blocks
-    int vec_threads = 256;  // their CTA size
+    int vec_threads = 32;   // their CTA size (3-component rows)
+    int vec_threads_p = 128;  // ... and for the 1-component pressure rows
+    int df_threads = 32;    // CTA size of the lane-group double-float kernels
     int use_chunk = 0;    // threads per CTA of the chunked row schedule, 0 = off
     nm::DevBuf sched;   // int [nreg] region counters
     int nreg = 0;

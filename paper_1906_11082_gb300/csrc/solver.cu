@@ -90,6 +90,7 @@ static void set_sched(KronArgs<T>& a, nm_problem* P) {
     a.chunk = P->use_chunk;
     a.vec = P->use_vec;
     a.vec_threads = P->vec_threads;
+    a.vec_threads_p = P->vec_threads_p;
     if (P->use_sched && P->sched.p) {
         a.sched = P->sched.as<int>();
         a.nreg = P->nreg;
@@ -396,6 +397,9 @@ static int cheb32(nm_problem* P, const DevCSR& A, int R, int b, int k, double lo
     NM_TRY(launch_dscale<float>(R, nodes, b, (float)cc.inv_theta, A.dinv32.as<float>(), w, b, xa, b, s));
     float* buf[2] = {xb, xa};
     double om = 2.0;
+    // profile kind 2: the float mass-matrix semi-iteration launches alone
+    cudaEvent_t ev = nullptr;
+    if (R == 3) NM_TRY(prof_begin(P, s, &ev));
     for (int j = 2; j <= k; ++j) {
         om = 1.0 / (1.0 - om / cc.four_sig2);
         KronArgs<float> a;
@@ -419,6 +423,7 @@ static int cheb32(nm_problem* P, const DevCSR& A, int R, int b, int k, double lo
         a.inv_theta = (float)cc.inv_theta;
         NM_TRY(launch_kron<float>(R, KRON_CHEB, a, s));
     }
+    if (R == 3) NM_TRY(prof_end(P, s, 2, ev, k - 1));
     return NM_OK;
 }
 
@@ -431,7 +436,7 @@ static int mixed_solve(nm_problem* P, const DevCSR& A, int R, int b, int k, cons
     NM_TRY(cheb32(P, A, R, b, k, kMassLo, kMassHi, S.w32, S.xa, S.xb, S.xs, s));
     if (df)
         NM_TRY(launch_resid_df(R, A.nrows, A.rowptr.as<int>(), A.col.as<int>(), A.val32.as<float>(),
-                               A.vlo32.as<float>(), W, ldw, S.xs, S.w32, b, s, P->use_vec));
+                               A.vlo32.as<float>(), W, ldw, S.xs, S.w32, b, s, P->use_vec, P->df_threads));
     else
         NM_TRY(launch_resid_mixed(R, A.nrows, A.rowptr.as<int>(), A.col.as<int>(), A.val.as<double>(), W, ldw,
                                   S.xs, S.w32, b, s));
@@ -498,6 +503,7 @@ static int apply_K_mixed(nm_problem* P, const double* X, int64_t ldx, double* W,
     f.W = W;
     f.ldw = ldw;
     f.vec = P->use_vec;
+    f.nt = P->df_threads;
     return launch_bsr33_df(f, s);
 }
 
