@@ -133,6 +133,12 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the float
+# mass-step kernel (kron_v4_kernel<3, 1, 32>) on this workload, from the ncu
+# capture summarised in profiles/kron_v4_mass_step_planet_h0.05_b32.md
+# (same matrices and block width as the timed launches).
+V4_TRAFFIC_BYTES = 543_801_344 + 123_877_376
+
 # FP64 peak of GB300 (NVIDIA's published B300 figure, 1.25 TFLOP/s; equal to
 # 152 SMs x ~2.05 GHz x 2 FP64 FMA per SM per clock x 2 flop).
 FP64_PEAK_TFLOPS = 1.25
@@ -376,8 +382,9 @@ def run_ours(args):
                 "peak_source": "GB300 FP64 nominal (152 SM x 2 FMA/clk x 2.05 GHz)"}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": peak_hbm, "unit": "GB/s",
-                "frac": (gbs / peak_hbm) if gbs else None, "traffic": None,
-                "kernel": "kron_warp_kernel<double, 3, 1, 1>" if s == 8 else "kron_v4_kernel<3, 1, 256>",
+                "frac": (gbs / peak_hbm) if gbs else None,
+                "traffic": V4_TRAFFIC_BYTES if (s == 4 and args.h == H_MESH) else None,
+                "kernel": "kron_warp_kernel<double, 3, 1, 1>" if s == 8 else "kron_v4_kernel<3, 1, 32>",
                 "peak_source": f"{peak_src} copy bandwidth"}
     roof["bytes_per_launch"] = mbytes
     roof["flops_per_launch"] = mflops

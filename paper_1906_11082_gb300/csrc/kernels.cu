@@ -907,6 +907,31 @@ __global__ void convert_kernel(int64_t rows, int b, const Tin* X, int64_t ldx, T
     }
 }
 
+// w32 = float(W) and the first semi-iteration step x1 = inv_theta D^-1 w32
+// in one pass (the same float expression as dscale_kernel).
+__global__ void convert_x1_kernel(int R, int64_t nodes, int b, const double* W, int64_t ldw, float* w32,
+                                  float inv_theta, const float* dinv, float* x1) {
+    const int64_t total = (int64_t)R * nodes * b;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / b;
+        const int c = (int)(t - r * b);
+        const float w = (float)W[r * ldw + c];
+        w32[t] = w;
+        x1[t] = inv_theta * dinv[r / R] * w;
+    }
+}
+
+int launch_convert_x1(int R, int64_t nodes, int b, const double* W, int64_t ldw, float* w32, float inv_theta,
+                      const float* dinv, float* x1, cudaStream_t s) {
+    const int64_t total = (int64_t)R * nodes * b;
+    if (total == 0) return NM_OK;
+    convert_x1_kernel<<<grid_for(total), kThreads, 0, s>>>(R, nodes, b, W, ldw, w32, inv_theta, dinv, x1);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
 template <typename Tin, typename Tout>
 int launch_convert(int64_t rows, int b, const Tin* X, int64_t ldx, Tout* Y, int64_t ldy,
                    cudaStream_t s) {
@@ -1080,6 +1105,11 @@ __global__ void combine_kernel(const CombineArgs a) {
         const double tp = a.Tp ? a.Tp[t] : 0.0;
         const double tn = a.a1 * (sv - a.cshift * a.Tk[t]) - a.a2 * tp;
         a.Tn[t] = tn;
+        if (a.Th) {   // exact float pair of tn for the next double-float K_eff SpMM
+            const float h = __double2float_rn(tn);
+            a.Th[t] = h;
+            a.Tl[t] = __double2float_rn(tn - (double)h);
+        }
         if (a.Z) {
             const int64_t i = t / a.b;
             const int c = (int)(t - i * a.b);
@@ -1336,7 +1366,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) resid_df_v4_kernel(int64_t node
                                                                   const float* __restrict__ vh,
                                                                   const float* __restrict__ vl,
                                                                   const double* __restrict__ W, int64_t ldw,
-                                                                  const float* __restrict__ x, float* r) {
+                                                                  const float* __restrict__ x, float* r,
+                                                                  const float* __restrict__ dinv, float inv_theta,
+                                                                  float* x1) {
     const int lane = threadIdx.x & 31;
     const int g = lane >> 3, q = lane & 7;
     const int64_t row = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
@@ -1374,6 +1406,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) resid_df_v4_kernel(int64_t node
         out[c] = (float)((wp[c] - (double)h) - (double)l);
     }
     reinterpret_cast<float4*>(r + rr * 32)[q] = make_float4(out[0], out[1], out[2], out[3]);
+    if (x1) {   // first semi-iteration step on r, as dscale_kernel computes it
+        const float d = inv_theta * dinv[row];
+        reinterpret_cast<float4*>(x1 + rr * 32)[q] = make_float4(d * out[0], d * out[1], d * out[2], d * out[3]);
+    }
 }
 
 int launch_split(int64_t rows, int b, const double* X, int64_t ldx, float* Xh, float* Xl, cudaStream_t s) {
@@ -1415,13 +1451,15 @@ int launch_bsr33_df(const Bsr33DfArgs& a, cudaStream_t s) {
 
 int launch_resid_df(int R, int64_t nodes, const int* rowptr, const int* col, const float* vh, const float* vl,
                     const double* W, int64_t ldw, const float* x32, float* r32, int b, cudaStream_t s, int vec,
-                    int nt) {
+                    int nt, const float* dinv, float inv_theta, float* x1) {
     if (b < 1 || b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
-    if (vec && b == 32 && (((uintptr_t)x32 | (uintptr_t)r32) & 15) == 0) {
+    if (vec && b == 32 && (((uintptr_t)x32 | (uintptr_t)r32 | (uintptr_t)x1) & 15) == 0) {
         if (nt != 32 && nt != 64 && nt != 128) nt = 256;
         const int64_t grid = (nodes + nt / 32 - 1) / (nt / 32);
         if (grid == 0) return NM_OK;
-#define NM_RESID_V4(RR, NN) resid_df_v4_kernel<RR, NN><<<(unsigned)grid, NN, 0, s>>>(nodes, rowptr, col, vh, vl, W, ldw, x32, r32)
+#define NM_RESID_V4(RR, NN) \
+    resid_df_v4_kernel<RR, NN><<<(unsigned)grid, NN, 0, s>>>(nodes, rowptr, col, vh, vl, W, ldw, x32, r32, dinv, \
+                                                            inv_theta, x1)
         if (R == 3) {
             switch (nt) {
                 case 32: NM_RESID_V4(3, 32); break;
@@ -1456,6 +1494,7 @@ int launch_resid_df(int R, int64_t nodes, const int* rowptr, const int* col, con
         resid_df_kernel<1, 2><<<(unsigned)grid, kThreads, 0, s>>>(nodes, rowptr, col, vh, vl, W, ldw, x32, r32, b, shift);
     count_launch();
     NM_CUDA(cudaGetLastError());
+    if (x1) return launch_dscale<float>(R, nodes, b, inv_theta, dinv, r32, b, x1, b, s);
     return NM_OK;
 }
 

@@ -132,6 +132,8 @@ struct CombineArgs {
     double a1 = 0, cshift = 0, a2 = 0, gam = 0;
     const double* gam_tab = nullptr;   // per column group gamma (overrides gam)
     int gam_group = 1;
+    float* Th = nullptr;   // optional exact float pair (hi, lo) of Tn, dense
+    float* Tl = nullptr;
 };
 int launch_combine(const CombineArgs& a, cudaStream_t s);
 
@@ -165,7 +167,13 @@ int launch_bsr33_df(const Bsr33DfArgs& a, cudaStream_t s);
 // sums; x32 and r32 dense (ld b). vec: lane-group kernel when b = 32.
 int launch_resid_df(int R, int64_t nodes, const int* rowptr, const int* col, const float* vh, const float* vl,
                     const double* W, int64_t ldw, const float* x32, float* r32, int b, cudaStream_t s,
-                    int vec = 1, int nt = 256);
+                    int vec = 1, int nt = 256, const float* dinv = nullptr, float inv_theta = 0.f,
+                    float* x1 = nullptr);
+// With x1 != nullptr also writes the first semi-iteration step on r32,
+// x1 = inv_theta D^-1 r32 (dinv per node, ld b).
+// w32 = float(W) and x1 = inv_theta D^-1 w32 in one pass (w32, x1 dense).
+int launch_convert_x1(int R, int64_t nodes, int b, const double* W, int64_t ldw, float* w32, float inv_theta,
+                      const float* dinv, float* x1, cudaStream_t s);
 
 // Y[i, c] = alpha * X[i, c] (rows x b, row-major with leading dims).
 template <typename T>

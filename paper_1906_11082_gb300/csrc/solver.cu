@@ -390,11 +390,13 @@ static int get_mix_scratch(nm_problem* P, int b, MixScratch& S) {
 // k steps of float Jacobi-Chebyshev semi-iteration for (A (x) I_R) x = w;
 // w, xa, xb, xout: (R nodes) x b floats with ld b, xout distinct from xa, xb.
 static int cheb32(nm_problem* P, const DevCSR& A, int R, int b, int k, double lo, double hi, const float* w,
-                  float* xa, float* xb, float* xout, cudaStream_t s) {
+                  float* xa, float* xb, float* xout, cudaStream_t s, bool x1_ready = false) {
     const ChebCoef cc(lo, hi);
     const int64_t nodes = A.nrows;
     if (k == 1) return launch_dscale<float>(R, nodes, b, (float)cc.inv_theta, A.dinv32.as<float>(), w, b, xout, b, s);
-    NM_TRY(launch_dscale<float>(R, nodes, b, (float)cc.inv_theta, A.dinv32.as<float>(), w, b, xa, b, s));
+    // x1_ready: the producer of w already wrote the first step into xa
+    if (!x1_ready)
+        NM_TRY(launch_dscale<float>(R, nodes, b, (float)cc.inv_theta, A.dinv32.as<float>(), w, b, xa, b, s));
     float* buf[2] = {xb, xa};
     double om = 2.0;
     // profile kind 2: the float mass-matrix semi-iteration launches alone
@@ -432,23 +434,36 @@ static int cheb32(nm_problem* P, const DevCSR& A, int R, int b, int k, double lo
 static int mixed_solve(nm_problem* P, const DevCSR& A, int R, int b, int k, const double* W, int64_t ldw,
                        const MixScratch& S, bool df, cudaStream_t s) {
     const int64_t rows = R * A.nrows;
-    NM_TRY((launch_convert<double, float>(rows, b, W, ldw, S.w32, b, s)));
-    NM_TRY(cheb32(P, A, R, b, k, kMassLo, kMassHi, S.w32, S.xa, S.xb, S.xs, s));
-    if (df)
-        NM_TRY(launch_resid_df(R, A.nrows, A.rowptr.as<int>(), A.col.as<int>(), A.val32.as<float>(),
-                               A.vlo32.as<float>(), W, ldw, S.xs, S.w32, b, s, P->use_vec, P->df_threads));
+    const ChebCoef cc(kMassLo, kMassHi);
+    const float it = (float)cc.inv_theta;
+    // k >= 2: the float conversion of W and the double-float residual also
+    // write the first semi-iteration step, so cheb32 starts at step 2
+    const bool fuse = k >= 2;
+    if (fuse)
+        NM_TRY(launch_convert_x1(R, A.nrows, b, W, ldw, S.w32, it, A.dinv32.as<float>(), S.xa, s));
     else
+        NM_TRY((launch_convert<double, float>(rows, b, W, ldw, S.w32, b, s)));
+    NM_TRY(cheb32(P, A, R, b, k, kMassLo, kMassHi, S.w32, S.xa, S.xb, S.xs, s, fuse));
+    bool x1 = false;
+    if (df) {
+        NM_TRY(launch_resid_df(R, A.nrows, A.rowptr.as<int>(), A.col.as<int>(), A.val32.as<float>(),
+                               A.vlo32.as<float>(), W, ldw, S.xs, S.w32, b, s, P->use_vec, P->df_threads,
+                               A.dinv32.as<float>(), it, fuse ? S.xa : nullptr));
+        x1 = fuse;
+    } else {
         NM_TRY(launch_resid_mixed(R, A.nrows, A.rowptr.as<int>(), A.col.as<int>(), A.val.as<double>(), W, ldw,
                                   S.xs, S.w32, b, s));
-    return cheb32(P, A, R, b, k, kMassLo, kMassHi, S.w32, S.xa, S.xb, S.es, s);
+    }
+    return cheb32(P, A, R, b, k, kMassLo, kMassHi, S.w32, S.xa, S.xb, S.es, s, x1);
 }
 
 // W = K_eff X in double with the pressure inverse by a refined solve.
 static int apply_K_mixed(nm_problem* P, const double* X, int64_t ldx, double* W, int64_t ldw, int b, int k_P,
-                         const MixScratch& S, cudaStream_t s) {
+                         const MixScratch& S, cudaStream_t s, bool pre_split = false) {
     Mats<double> m = mats<double>(P);
     const bool df = P->use_df != 0;
-    if (df) NM_TRY(launch_split(P->info.n, b, X, ldx, S.Th, S.Tl, s));
+    // pre_split: S.Th / S.Tl already hold the exact float pair of X
+    if (df && !pre_split) NM_TRY(launch_split(P->info.n, b, X, ldx, S.Th, S.Tl, s));
     Bsr33Args<double> a;
     a.nrows = (int)m.Nu;
     a.rowptr = m.u_rp;
@@ -534,7 +549,7 @@ static int filter_apply_mixed(nm_problem* P, const nm_filter* f, const double* Y
     for (int k = 0; k < d; ++k) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         NM_TRY(prof_begin(P, s, &e0));
-        NM_TRY(apply_K_mixed(P, cur, b, S.W, b, b, f->k_P, S, s));
+        NM_TRY(apply_K_mixed(P, cur, b, S.W, b, b, f->k_P, S, s, k > 0 && P->use_df));
         NM_TRY(prof_end(P, s, 1, e0, kl));
         NM_TRY(prof_begin(P, s, &e1));
         NM_TRY(mixed_solve(P, P->Mr, 3, b, f->k_M, S.W, b, S, P->use_df != 0, s));
@@ -555,6 +570,10 @@ static int filter_apply_mixed(nm_problem* P, const nm_filter* f, const double* Y
         if (gt) {
             c.gam_tab = gt->dev + (int64_t)(k + 1) * gt->S;
             c.gam_group = gt->group;
+        }
+        if (P->use_df && k + 1 < d) {   // the next degree's K_eff SpMM takes Tn split
+            c.Th = S.Th;
+            c.Tl = S.Tl;
         }
         NM_TRY(launch_combine(c, s));
         NM_TRY(prof_end(P, s, 0, e1, 2 * f->k_M + 3));
