@@ -194,7 +194,11 @@ int nm_problem_export(const nm_problem* prob, int which, int64_t* nrows, int64_t
  * 1-component pressure rows: larger CTAs put more consecutive rows on one
  * SM's L1, smaller ones free their slot sooner when a CTA's rows differ in
  * length. key "df_threads" (32 default, 64, 128, 256): CTA size of the
- * NM_MIXED form's lane-group double-float SpMMs (b = 32). key "tile_rows": height of the row
+ * NM_MIXED form's lane-group double-float SpMMs (b = 32). key "overlap":
+ * 1 runs the mixed-form K_eff's fluid pressure chain (E_G^T X, the refined
+ * A_p solve) on a high-priority second stream of the problem while the A_G
+ * product runs on the caller's stream, then adds E_G S; 0 (default) runs
+ * them in sequence with E_G S fused into the A_G product. key "tile_rows": height of the row
  * tiles whose gathered operand the float kernels stage in shared memory
  * (0, the default, disables staging; 4..64, power of two); the tiles are
  * rebuilt on the host. key "tile_kernel": 1 or 2, the staged kernel

@@ -1118,6 +1118,39 @@ __global__ void combine_kernel(const CombineArgs a) {
     }
 }
 
+// W[3i + m, c] += sum_f E[f, m] S[col(f), c] for the 3x1-block CSR E over
+// u-node rows (the fluid coupling of K_eff), in double; one warp per row,
+// rows without entries return at once.
+__global__ void bsr31_add_kernel(int nrows, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                 const double* __restrict__ val, const double* __restrict__ S, int64_t lds, int b,
+                                 double* W, int64_t ldw) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (row >= nrows) return;
+    const int f0 = __ldg(rowptr + row), f1 = __ldg(rowptr + row + 1);
+    if (f0 == f1) return;
+    for (int c = lane; c < b; c += 32) {
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int f = f0; f < f1; ++f) {
+            const double sv = __ldg(S + (int64_t)__ldg(col + f) * lds + c);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) acc[m] += __ldg(val + 3 * (int64_t)f + m) * sv;
+        }
+#pragma unroll
+        for (int m = 0; m < 3; ++m) W[(3 * row + m) * ldw + c] += acc[m];
+    }
+}
+
+int launch_bsr31_add(int nrows, const int* rowptr, const int* col, const double* val, const double* S, int64_t lds,
+                     int b, double* W, int64_t ldw, cudaStream_t s) {
+    const int64_t grid = (nrows + kThreads / 32 - 1) / (kThreads / 32);
+    if (grid == 0) return NM_OK;
+    bsr31_add_kernel<<<(unsigned)grid, kThreads, 0, s>>>(nrows, rowptr, col, val, S, lds, b, W, ldw);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
 int launch_combine(const CombineArgs& a, cudaStream_t s) {
     if (a.rows * a.b == 0) return NM_OK;
     combine_kernel<<<grid_for(a.rows * a.b), kThreads, 0, s>>>(a);

@@ -136,6 +136,10 @@ struct CombineArgs {
     float* Tl = nullptr;
 };
 int launch_combine(const CombineArgs& a, cudaStream_t s);
+// W[3i + m, c] += sum_f E[f, m] S[col(f), c]: the fluid coupling term of
+// K_eff added to a finished A_G product (3x1-block CSR over u-node rows).
+int launch_bsr31_add(int nrows, const int* rowptr, const int* col, const double* val, const double* S, int64_t lds,
+                     int b, double* W, int64_t ldw, cudaStream_t s);
 
 // Double-float forms (value = hi + lo, two floats, ~2^-48 relative): the
 // K_eff SpMM and the refinement residual on the float units.

@@ -146,6 +146,17 @@ struct nm_problem {
     // scratch for the filter recurrence
     nm::Workspace ws;
     nm::DevBuf pscratch;     // pressure-sized scratch for the Schur term
+    // mixed-form K_eff: the fluid pressure chain runs on `aux` (high
+    // priority) while A_G X runs on the caller's stream (option "overlap")
+    int overlap = 0;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    ~nm_problem() {
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (aux) cudaStreamDestroy(aux);
+    }
 };
 
 namespace nm {

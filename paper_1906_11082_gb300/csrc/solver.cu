@@ -474,6 +474,23 @@ static int apply_K_mixed(nm_problem* P, const double* X, int64_t ldx, double* W,
     a.ldx = ldx;
     a.W = W;
     a.ldw = ldw;
+    // With "overlap", the pressure chain (E_G^T X, the refined A_p solve,
+    // the combine) runs on the problem's high-priority aux stream while the
+    // A_G product runs on s; E_G S is added after the join.
+    const bool split_e = m.Np > 0 && P->overlap;
+    cudaStream_t ps = s;
+    if (split_e) {
+        if (!P->aux) {
+            int lo_pri = 0, hi_pri = 0;
+            NM_CUDA(cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri));
+            NM_CUDA(cudaStreamCreateWithPriority(&P->aux, cudaStreamNonBlocking, hi_pri));
+            NM_CUDA(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+            NM_CUDA(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+        }
+        ps = P->aux;
+        NM_CUDA(cudaEventRecord(P->ev_fork, s));
+        NM_CUDA(cudaStreamWaitEvent(ps, P->ev_fork, 0));
+    }
     if (m.Np > 0) {
         Bsr13Args<double> q;
         q.nrows = (int)m.Np;
@@ -485,20 +502,45 @@ static int apply_K_mixed(nm_problem* P, const double* X, int64_t ldx, double* W,
         q.ldx = ldx;
         q.Q = S.Q64;
         q.ldq = b;
-        NM_TRY(launch_bsr13<double>(q, s));
-        NM_TRY(mixed_solve(P, P->Pn, 1, b, k_P, S.Q64, b, S, P->use_df != 0, s));
+        NM_TRY(launch_bsr13<double>(q, ps));
+        NM_TRY(mixed_solve(P, P->Pn, 1, b, k_P, S.Q64, b, S, P->use_df != 0, ps));
         CombineArgs c;
         c.rows = m.Np;
         c.b = b;
         c.x32 = S.xs;
         c.e32 = S.es;
         c.out = S.S64;
-        NM_TRY(launch_combine(c, s));
-        a.e_rowptr = m.e_rp;
-        a.e_col = m.e_col;
-        a.e_val = m.EG;
-        a.S = S.S64;
-        a.lds = b;
+        NM_TRY(launch_combine(c, ps));
+        if (!split_e) {
+            a.e_rowptr = m.e_rp;
+            a.e_col = m.e_col;
+            a.e_val = m.EG;
+            a.S = S.S64;
+            a.lds = b;
+        }
+    }
+    if (split_e) {
+        NM_CUDA(cudaEventRecord(P->ev_join, ps));
+        if (!df) {
+            NM_TRY(launch_bsr33<double>(a, s));
+        } else {
+            Bsr33DfArgs f;
+            f.nrows = a.nrows;
+            f.rowptr = a.rowptr;
+            f.col = a.col;
+            f.vh = P->AG.val32.as<float>();
+            f.vl = P->AG.vlo32.as<float>();
+            f.Xh = S.Th;
+            f.Xl = S.Tl;
+            f.b = b;
+            f.W = W;
+            f.ldw = ldw;
+            f.vec = P->use_vec;
+            f.nt = P->df_threads;
+            NM_TRY(launch_bsr33_df(f, s));
+        }
+        NM_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));
+        return launch_bsr31_add((int)m.Nu, m.e_rp, m.e_col, m.EG, S.S64, b, b, W, ldw, s);
     }
     if (!df) return launch_bsr33<double>(a, s);
     Bsr33DfArgs f;
