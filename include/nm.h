@@ -198,7 +198,12 @@ int nm_problem_export(const nm_problem* prob, int which, int64_t* nrows, int64_t
  * 1 runs the mixed-form K_eff's fluid pressure chain (E_G^T X, the refined
  * A_p solve) on a high-priority second stream of the problem while the A_G
  * product runs on the caller's stream, then adds E_G S; 0 (default) runs
- * them in sequence with E_G S fused into the A_G product. key "tile_rows": height of the row
+ * them in sequence with E_G S fused into the A_G product. key "graphs": 1
+ * replays degrees 1..d-1 of the NM_MIXED filter recurrence from two
+ * captured CUDA graphs (odd / even degree; gamma_{k+1} read on the device
+ * at a device-side degree counter), on streams other than the legacy
+ * default stream and when profiling is off; results are identical to the
+ * eager launches. 0 (default) launches every kernel from the host. key "tile_rows": height of the row
  * tiles whose gathered operand the float kernels stage in shared memory
  * (0, the default, disables staging; 4..64, power of two); the tiles are
  * rebuilt on the host. key "tile_kernel": 1 or 2, the staged kernel
@@ -213,6 +218,7 @@ int nm_set_option(nm_problem* prob, const char* key, int64_t value);
 /* Autotuner: times one degree of the filter recurrence (precision prec,
  * block width b, inner steps k_M) on this problem for every kernel variant
  * of the options above ("sched", "chunk", "vec", "tile_rows"/"tile_kernel", and for
+ * NM_MIXED "graphs" and
  * NM_MIXED "double_float"), keeps the fastest, and reports the time per
  * column and degree of block widths 16, 32 and 64 with it. All variants
  * compute the same sums (up to rounding order). report: caller buffer

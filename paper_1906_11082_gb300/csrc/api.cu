@@ -229,6 +229,11 @@ int nm_set_option(nm_problem* P, const char* key, int64_t value) {
         (std::string(key) == "vec_threads" ? P->vec_threads : P->vec_threads_p) = (int)value;
         return NM_OK;
     }
+    if (std::string(key) == "graphs") {
+        if (value != 0 && value != 1) return fail(NM_EINVAL, "graphs must be 0 or 1");
+        P->use_graphs = (int)value;
+        return NM_OK;
+    }
     if (std::string(key) == "overlap") {
         if (value != 0 && value != 1) return fail(NM_EINVAL, "overlap must be 0 or 1");
         P->overlap = (int)value;

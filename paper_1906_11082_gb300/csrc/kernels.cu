@@ -1113,7 +1113,9 @@ __global__ void combine_kernel(const CombineArgs a) {
         if (a.Z) {
             const int64_t i = t / a.b;
             const int c = (int)(t - i * a.b);
-            a.Z[i * a.ldz + c] += (a.gam_tab ? a.gam_tab[c / a.gam_group] : a.gam) * tn;
+            const double gm = a.deg ? a.gam_tab[(int64_t)(a.deg[0] + 1) * a.gam_stride + c / a.gam_group]
+                                    : (a.gam_tab ? a.gam_tab[c / a.gam_group] : a.gam);
+            a.Z[i * a.ldz + c] += gm * tn;
         }
     }
 }
@@ -1146,6 +1148,23 @@ int launch_bsr31_add(int nrows, const int* rowptr, const int* col, const double*
     const int64_t grid = (nrows + kThreads / 32 - 1) / (kThreads / 32);
     if (grid == 0) return NM_OK;
     bsr31_add_kernel<<<(unsigned)grid, kThreads, 0, s>>>(nrows, rowptr, col, val, S, lds, b, W, ldw);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+__global__ void set_int_kernel(int* p, int v) { *p = v; }
+__global__ void inc_int_kernel(int* p) { *p += 1; }
+
+int launch_set_int(int* p, int v, cudaStream_t s) {
+    set_int_kernel<<<1, 1, 0, s>>>(p, v);
+    count_launch();
+    NM_CUDA(cudaGetLastError());
+    return NM_OK;
+}
+
+int launch_inc_int(int* p, cudaStream_t s) {
+    inc_int_kernel<<<1, 1, 0, s>>>(p);
     count_launch();
     NM_CUDA(cudaGetLastError());
     return NM_OK;

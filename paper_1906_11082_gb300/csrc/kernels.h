@@ -8,6 +8,7 @@ namespace nm {
 
 // Process-wide count of kernels launched by the library (nm_kernel_launches).
 void count_launch(uint64_t n = 1);
+uint64_t launches_so_far();
 
 enum KronMode { KRON_PLAIN = 0, KRON_CHEB = 1, KRON_CHEB_FILT = 2, KRON_CORI = 3 };
 
@@ -134,8 +135,17 @@ struct CombineArgs {
     int gam_group = 1;
     float* Th = nullptr;   // optional exact float pair (hi, lo) of Tn, dense
     float* Tl = nullptr;
+    // graph replay: gamma = gam_tab[(deg[0] + 1) * gam_stride + c / gam_group]
+    // with the degree read from device memory (overrides gam and gam_tab's
+    // host-side offset)
+    const int* deg = nullptr;
+    int gam_stride = 0;
 };
 int launch_combine(const CombineArgs& a, cudaStream_t s);
+// One-thread kernels that set / advance the device-side degree counter of
+// a replayed filter graph.
+int launch_set_int(int* p, int v, cudaStream_t s);
+int launch_inc_int(int* p, cudaStream_t s);
 // W[3i + m, c] += sum_f E[f, m] S[col(f), c]: the fluid coupling term of
 // K_eff added to a finished A_G product (3x1-block CSR over u-node rows).
 int launch_bsr31_add(int nrows, const int* rowptr, const int* col, const double* val, const double* S, int64_t lds,

@@ -149,6 +149,11 @@ struct nm_problem {
     // mixed-form K_eff: the fluid pressure chain runs on `aux` (high
     // priority) while A_G X runs on the caller's stream (option "overlap")
     int overlap = 0;
+    // mixed-form filter degrees 1..d-1 replayed as two captured CUDA graphs
+    // (option "graphs"): gamma table and degree counter live on the device
+    int use_graphs = 0;
+    nm::DevBuf graph_gam;   // (degree + 1) doubles
+    nm::DevBuf graph_deg;   // one int
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~nm_problem() {

@@ -585,10 +585,12 @@ static int filter_apply_mixed(nm_problem* P, const nm_filter* f, const double* Y
     }
     if (d == 0) return NM_OK;
     NM_TRY(launch_scale_copy<double>(n, b, 1.0, Y, ldy, S.TA, b, s));
-    double* cur = S.TA;
-    double* prev = S.TB;
     const int64_t kl = 1 + (P->info.Np > 0 ? 2 * f->k_P + 4 : 0);
-    for (int k = 0; k < d; ++k) {
+    // One degree k of the recurrence (T_k in cur, T_{k-1} in prev; T_{k+1}
+    // overwrites prev). With dev_gam the combine takes gamma_{k+1} from the
+    // device table at the device-side degree counter (graph replay).
+    auto degree = [&](int k, double* cur, double* prev, const double* dev_gam, int gstride, int ggroup,
+                      const int* ctr) -> int {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         NM_TRY(prof_begin(P, s, &e0));
         NM_TRY(apply_K_mixed(P, cur, b, S.W, b, b, f->k_P, S, s, k > 0 && P->use_df));
@@ -608,19 +610,99 @@ static int filter_apply_mixed(nm_problem* P, const nm_filter* f, const double* Y
         c.a1 = (k == 0 ? 1.0 : 2.0) / f->e;
         c.cshift = f->c;
         c.a2 = k == 0 ? 0.0 : 1.0;
-        c.gam = gt ? 0.0 : f->gamma[k + 1];
-        if (gt) {
-            c.gam_tab = gt->dev + (int64_t)(k + 1) * gt->S;
-            c.gam_group = gt->group;
+        if (dev_gam) {
+            c.gam_tab = dev_gam;
+            c.gam_stride = gstride;
+            c.gam_group = ggroup;
+            c.deg = ctr;
+        } else {
+            c.gam = gt ? 0.0 : f->gamma[k + 1];
+            if (gt) {
+                c.gam_tab = gt->dev + (int64_t)(k + 1) * gt->S;
+                c.gam_group = gt->group;
+            }
         }
-        if (P->use_df && k + 1 < d) {   // the next degree's K_eff SpMM takes Tn split
+        if (P->use_df && (dev_gam || k + 1 < d)) {   // the next degree's K_eff SpMM takes Tn split
             c.Th = S.Th;
             c.Tl = S.Tl;
         }
         NM_TRY(launch_combine(c, s));
         NM_TRY(prof_end(P, s, 0, e1, 2 * f->k_M + 3));
-        std::swap(cur, prev);
+        return NM_OK;
+    };
+    const bool graphs = P->use_graphs && !P->profile && !P->overlap && s != nullptr && d >= 3;
+    if (!graphs) {
+        double* cur = S.TA;
+        double* prev = S.TB;
+        for (int k = 0; k < d; ++k) {
+            NM_TRY(degree(k, cur, prev, nullptr, 0, 1, nullptr));
+            std::swap(cur, prev);
+        }
+        return NM_OK;
     }
+    // Graph replay of degrees 1..d-1 (the d x k_M launch chain): degree 0
+    // runs eagerly; odd and even degrees differ only in which block holds
+    // T_k, so two captured graphs serve them all, with gamma_{k+1} read
+    // from a device table at a device-side degree counter that each graph
+    // advances at its end.
+    NM_TRY(degree(0, S.TA, S.TB, nullptr, 0, 1, nullptr));
+    const double* gtab;
+    int gstride, ggroup;
+    if (gt) {
+        gtab = gt->dev;
+        gstride = gt->S;
+        ggroup = gt->group;
+    } else {
+        const size_t gbytes = (size_t)(d + 1) * sizeof(double);
+        if (P->graph_gam.bytes < gbytes) NM_TRY(P->graph_gam.alloc(gbytes));
+        NM_CUDA(cudaMemcpyAsync(P->graph_gam.p, f->gamma, gbytes, cudaMemcpyHostToDevice, s));
+        gtab = P->graph_gam.as<double>();
+        gstride = 1;
+        ggroup = b;
+    }
+    if (!P->graph_deg.p) NM_TRY(P->graph_deg.alloc(sizeof(int)));
+    int* ctr = P->graph_deg.as<int>();
+    NM_TRY(launch_set_int(ctr, 1, s));
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    uint64_t nodes[2] = {0, 0};
+    auto drop = [&]() {
+        for (auto& x : exec)
+            if (x) cudaGraphExecDestroy(x);
+    };
+    for (int par = 0; par < 2; ++par) {   // par 0: odd degrees (T_k in TB), par 1: even
+        double* cur = par == 0 ? S.TB : S.TA;
+        double* prev = par == 0 ? S.TA : S.TB;
+        const uint64_t l0 = launches_so_far();
+        NM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int rc = degree(par == 0 ? 1 : 2, cur, prev, gtab, gstride, ggroup, ctr);
+        if (rc == NM_OK) rc = launch_inc_int(ctr, s);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(s, &g);
+        nodes[par] = launches_so_far() - l0;
+        count_launch((uint64_t)0 - nodes[par]);   // captured, not launched
+        if (rc != NM_OK || ec != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            drop();
+            cudaGetLastError();
+            return rc != NM_OK ? rc : fail(NM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&exec[par], g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            drop();
+            return fail(NM_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+        }
+    }
+    for (int k = 1; k < d; ++k) {
+        const int par = (k & 1) ? 0 : 1;
+        const cudaError_t el = cudaGraphLaunch(exec[par], s);
+        if (el != cudaSuccess) {
+            drop();
+            return fail(NM_ECUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(el));
+        }
+        count_launch(nodes[par]);
+    }
+    drop();   // released once the launched graphs complete
     return NM_OK;
 }
 
@@ -896,20 +978,21 @@ int autotune(nm_problem* P, int b, nm_prec prec, int k_M, std::string* report) {
     } else {
         NM_TRY(launch_philox_normal(n * 64, 7, Y.as<double>(), s));
     }
-    struct Cfg { int sched, tile, tk, df, chunk, vec; };
+    struct Cfg { int sched, tile, tk, df, chunk, vec, graphs; };
     std::vector<Cfg> cfgs;
     const int df1 = prec == NM_MIXED ? 1 : P->use_df;
     for (int sched : {0, 1})
         for (int df : (prec == NM_MIXED ? std::vector<int>{1, 0} : std::vector<int>{P->use_df}))
-            cfgs.push_back({sched, 0, 2, df, 0, 1});
-    if (prec != NM_F64 && b == 32) cfgs.push_back({0, 0, 2, df1, 0, 0});
+            cfgs.push_back({sched, 0, 2, df, 0, 1, 0});
+    if (prec == NM_MIXED) cfgs.push_back({0, 0, 2, 1, 0, 1, 1});
+    if (prec != NM_F64 && b == 32) cfgs.push_back({0, 0, 2, df1, 0, 0, 0});
     if (b >= 17)
-        for (int ch : {256, 512, 1024}) cfgs.push_back({0, 0, 2, df1, ch, 0});
+        for (int ch : {256, 512, 1024}) cfgs.push_back({0, 0, 2, df1, ch, 0, 0});
     if (prec != NM_F64 && b == 32) {
-        cfgs.push_back({0, 16, 2, df1, 0, 0});
-        cfgs.push_back({0, 32, 2, df1, 0, 0});
+        cfgs.push_back({0, 16, 2, df1, 0, 0, 0});
+        cfgs.push_back({0, 32, 2, df1, 0, 0, 0});
     }
-    const int reps = 2;
+    const int reps = 6;   // degrees per timing (graph replay needs at least 3)
     double best = 1e300;
     Cfg bestc = cfgs[0];
     std::string rep = "{\"b\": " + std::to_string(b) + ", \"variants\": [";
@@ -919,6 +1002,7 @@ int autotune(nm_problem* P, int b, nm_prec prec, int k_M, std::string* report) {
         P->use_df = c.df;
         P->use_chunk = c.chunk;
         P->use_vec = c.vec;
+        P->use_graphs = c.graphs;
         NM_TRY(set_tile_rows(P, c.tile));
         if (c.tile) P->Mr.tile_kernel = P->Pn.tile_kernel = c.tk;
         double ms = 0;
@@ -926,9 +1010,9 @@ int autotune(nm_problem* P, int b, nm_prec prec, int k_M, std::string* report) {
         ms /= reps;
         char buf[160];
         snprintf(buf, sizeof buf,
-                 "%s{\"sched\": %d, \"chunk\": %d, \"vec\": %d, \"tile_rows\": %d, \"double_float\": %d, "
-                 "\"ms_per_degree\": %.4f}",
-                 i ? ", " : "", c.sched, c.chunk, c.vec, c.tile, c.df, ms);
+                 "%s{\"sched\": %d, \"chunk\": %d, \"vec\": %d, \"graphs\": %d, \"tile_rows\": %d, "
+                 "\"double_float\": %d, \"ms_per_degree\": %.4f}",
+                 i ? ", " : "", c.sched, c.chunk, c.vec, c.graphs, c.tile, c.df, ms);
         rep += buf;
         if (ms < best) {
             best = ms;
@@ -939,10 +1023,12 @@ int autotune(nm_problem* P, int b, nm_prec prec, int k_M, std::string* report) {
     P->use_df = bestc.df;
     P->use_chunk = bestc.chunk;
     P->use_vec = bestc.vec;
+    P->use_graphs = bestc.graphs;
     NM_TRY(set_tile_rows(P, bestc.tile));
     if (bestc.tile) P->Mr.tile_kernel = P->Pn.tile_kernel = bestc.tk;
     rep += "], \"chosen\": {\"sched\": " + std::to_string(bestc.sched) + ", \"chunk\": " +
-           std::to_string(bestc.chunk) + ", \"vec\": " + std::to_string(bestc.vec) + ", \"tile_rows\": " +
+           std::to_string(bestc.chunk) + ", \"vec\": " + std::to_string(bestc.vec) + ", \"graphs\": " +
+           std::to_string(bestc.graphs) + ", \"tile_rows\": " +
            std::to_string(bestc.tile) + ", \"double_float\": " + std::to_string(bestc.df) + "}, \"us_per_column_degree\": {";
     int first = 1;
     for (int bb : {16, 32, 64}) {

@@ -238,10 +238,13 @@ def test_lanczos_slice_ball_mixed(nm, ball):
 
 
 @pytest.mark.parametrize("k", [7, 28])
-def test_solve_M_mixed_matches_refined_oracle(nm, planet, k):
+@pytest.mark.parametrize("b", [6, 32])
+def test_solve_M_mixed_matches_refined_oracle(nm, planet, k, b):
+    """b = 32 runs the lane-group float and double-float kernels with the
+    fused first steps; b = 6 the generic ones."""
     mesh, model, S, P = planet
-    Wc = np.random.default_rng(k).standard_normal((S.n, 6))
-    X = torch.empty((S.n, 6), dtype=torch.float64, device=DEV)
+    Wc = np.random.default_rng(k).standard_normal((S.n, b))
+    X = torch.empty((S.n, b), dtype=torch.float64, device=DEV)
     P.solve_M(_dev(to_internal(P, Wc)), X, k_M=k, prec=nm.NM_MIXED)
     ref = filtlan.refined_solve(S.M, 1.0 / S.M.diagonal(), Wc, k)
     # float semi-iterations add ~6e-8 x |residual| of noise
@@ -249,25 +252,52 @@ def test_solve_M_mixed_matches_refined_oracle(nm, planet, k):
     assert rel_err(to_canonical(P, _host(X)), ref) <= tol
 
 
-def test_apply_K_mixed_matches_refined_oracle(nm, planet):
+@pytest.mark.parametrize("b,overlap", [(4, 0), (32, 0), (32, 1)])
+def test_apply_K_mixed_matches_refined_oracle(nm, planet, b, overlap):
+    """Also with the pressure chain on the problem's second stream
+    (option overlap)."""
     mesh, model, S, P = planet
-    Xc = np.random.default_rng(9).standard_normal((S.n, 4))
-    Y = torch.empty((S.n, 4), dtype=torch.float64, device=DEV)
-    P.apply_K(_dev(to_internal(P, Xc)), Y, k_P=28, prec=nm.NM_MIXED)
+    Xc = np.random.default_rng(9).standard_normal((S.n, b))
+    Y = torch.empty((S.n, b), dtype=torch.float64, device=DEV)
+    try:
+        P.set_option("overlap", overlap)
+        P.apply_K(_dev(to_internal(P, Xc)), Y, k_P=28, prec=nm.NM_MIXED)
+    finally:
+        P.set_option("overlap", 0)
     op = filtlan.Operator(S, k_M=28, k_P=28, refine=True)
     assert rel_err(to_canonical(P, _host(Y)), op.K(Xc)) <= 1e-11
 
 
-def test_filter_apply_mixed(nm, planet):
+@pytest.mark.parametrize("b,ld", [(8, 8), (32, 32), (32, 40)])
+def test_filter_apply_mixed(nm, planet, b, ld):
+    """b = 32 runs the lane-group kernels, the fused first steps and the
+    split carried by the combine; ld > b leaves the caller's blocks
+    non-dense (the recurrence's own blocks stay dense)."""
     mesh, model, S, P = planet
     op = filtlan.Operator(S, k_M=20, k_P=20, refine=True)
     lo, hi = filtlan.spectrum_bounds(op, S.n)
     gam, c, e = filtlan.filter_coeffs(lo, hi, 0.5, 9.0, 20)
-    Yc = np.random.default_rng(4).standard_normal((S.n, 8))
-    Z = torch.empty((S.n, 8), dtype=torch.float64, device=DEV)
-    P.filter_apply(gam, c, e, 20, _dev(to_internal(P, Yc)), Z, k_P=20, prec=nm.NM_MIXED)
+    Yc = np.random.default_rng(4).standard_normal((S.n, b))
+    Ybuf = torch.zeros((S.n, ld), dtype=torch.float64, device=DEV)
+    Ybuf[:, :b] = _dev(to_internal(P, Yc))
+    Zbuf = torch.full((S.n, ld), 7.0, dtype=torch.float64, device=DEV)
+    P.filter_apply(gam, c, e, 20, Ybuf[:, :b], Zbuf[:, :b], k_P=20, prec=nm.NM_MIXED)
     ref = filtlan.filter_apply(op, gam, c, e, Yc)
-    assert rel_err(to_canonical(P, _host(Z)), ref) <= 1e-8
+    assert rel_err(to_canonical(P, _host(Zbuf[:, :b])), ref) <= 1e-8
+    if ld > b:
+        assert bool((Zbuf[:, b:] == 7.0).all())     # padding columns untouched
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed", "f32"])
+def test_filter_degree_zero(nm, ball, prec):
+    """A degree-0 filter is gamma_0 Y, exactly."""
+    _, S, P = ball
+    dt = torch.float32 if prec == "f32" else torch.float64
+    Y = torch.randn((S.n, 5), dtype=dt, device=DEV)
+    Z = torch.empty_like(Y)
+    pr = {"f64": nm.NM_F64, "mixed": nm.NM_MIXED, "f32": nm.NM_F32}[prec]
+    P.filter_apply(np.array([0.375]), 0.0, 1.0, 4, Y, Z, prec=pr)
+    assert bool((Z == Y * 0.375).all())
 
 
 def _planet_slice_edges(lam, lo_skip=4, count=12):
@@ -476,6 +506,48 @@ def test_vec_option_agrees(nm, planet):
     assert rel_err(to_canonical(P, vec[2]), filtlan.filter_apply(op, gam, c, e, Wc)) <= 1e-3
     with pytest.raises(nm.NMError):
         P.set_option("vec", 2)
+
+
+@pytest.mark.parametrize("b", [8, 32])
+def test_graph_replay_matches_eager(nm, planet, b):
+    """Option graphs: degrees 1..d-1 of the mixed filter replayed from two
+    captured CUDA graphs (gamma and the degree read on the device) give the
+    eagerly launched result bit for bit."""
+    mesh, model, S, P = planet
+    lo, hi = P.spectrum_bounds(k_M=20)
+    gam, c, e = nm.filter_design(lo, hi, 0.5, 9.0, 9)
+    Y = _dev(np.random.default_rng(31).standard_normal((S.n, b)))
+    Z0, Z1 = torch.empty_like(Y), torch.empty_like(Y)
+    st = torch.cuda.Stream()           # capture needs a stream other than the legacy default
+    with torch.cuda.stream(st):
+        P.filter_apply(gam, c, e, 20, Y, Z0, prec=nm.NM_MIXED, stream=st)
+        n0 = nm.kernel_launches()
+        try:
+            P.set_option("graphs", 1)
+            P.filter_apply(gam, c, e, 20, Y, Z1, prec=nm.NM_MIXED, stream=st)
+        finally:
+            P.set_option("graphs", 0)
+        n1 = nm.kernel_launches()
+    st.synchronize()
+    assert torch.equal(Z0, Z1)
+    assert n1 - n0 > 9 * 40          # replayed kernels are counted
+
+
+def test_graph_replay_batched_slices(nm, ball):
+    """The batched recurrence (per-slice gamma table) under graph replay
+    gives the eager eigenvalues exactly."""
+    w, S, P = ball
+    out = []
+    for gflag in (0, 1):
+        P.set_option("graphs", gflag)
+        rs = P.lanczos_multi([(0.0, 2.7), (2.7, 3.0)], block=8, degree=100, k_M=20, k_P=20, max_blocks=16,
+                             prec=nm.NM_MIXED, seed=4)
+        out.append([r.lam.copy() for r in rs])
+        for r in rs:
+            r.free()
+    P.set_option("graphs", 0)
+    for a, b_ in zip(*out):
+        assert np.array_equal(a, b_) and len(a) > 0
 
 
 def test_autotune_report_and_results(nm, planet):
