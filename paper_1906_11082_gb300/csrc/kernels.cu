@@ -1170,8 +1170,64 @@ int launch_inc_int(int* p, cudaStream_t s) {
     return NM_OK;
 }
 
+// The same update two columns per thread (b even, operands 8/16-byte
+// aligned, Z's leading dimension even, rows * b / 2 < 2^30): 32-bit index
+// arithmetic, float2 / double2 accesses, identical arithmetic per element.
+__global__ void combine2_kernel(const CombineArgs a) {
+    const int hb = a.b >> 1;
+    const int total = (int)(a.rows * hb);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const float2 x = reinterpret_cast<const float2*>(a.x32)[t];
+        const float2 e = reinterpret_cast<const float2*>(a.e32)[t];
+        const double s0 = (double)x.x + (double)e.x, s1 = (double)x.y + (double)e.y;
+        if (!a.Tn) {
+            reinterpret_cast<double2*>(a.out)[t] = make_double2(s0, s1);
+            continue;
+        }
+        const double2 tk = reinterpret_cast<const double2*>(a.Tk)[t];
+        const double2 tp = a.Tp ? reinterpret_cast<const double2*>(a.Tp)[t] : make_double2(0.0, 0.0);
+        const double n0 = a.a1 * (s0 - a.cshift * tk.x) - a.a2 * tp.x;
+        const double n1 = a.a1 * (s1 - a.cshift * tk.y) - a.a2 * tp.y;
+        reinterpret_cast<double2*>(a.Tn)[t] = make_double2(n0, n1);
+        if (a.Th) {
+            const float h0 = __double2float_rn(n0), h1 = __double2float_rn(n1);
+            reinterpret_cast<float2*>(a.Th)[t] = make_float2(h0, h1);
+            reinterpret_cast<float2*>(a.Tl)[t] =
+                make_float2(__double2float_rn(n0 - (double)h0), __double2float_rn(n1 - (double)h1));
+        }
+        if (a.Z) {
+            const int i = t / hb;
+            const int c = 2 * (t - i * hb);
+            double g0, g1;
+            if (a.deg) {
+                const double* gt = a.gam_tab + (int64_t)(a.deg[0] + 1) * a.gam_stride;
+                g0 = gt[c / a.gam_group];
+                g1 = gt[(c + 1) / a.gam_group];
+            } else if (a.gam_tab) {
+                g0 = a.gam_tab[c / a.gam_group];
+                g1 = a.gam_tab[(c + 1) / a.gam_group];
+            } else {
+                g0 = g1 = a.gam;
+            }
+            double2* zp = reinterpret_cast<double2*>(a.Z + (int64_t)i * a.ldz + c);
+            double2 z = *zp;
+            z.x += g0 * n0;
+            z.y += g1 * n1;
+            *zp = z;
+        }
+    }
+}
+
 int launch_combine(const CombineArgs& a, cudaStream_t s) {
     if (a.rows * a.b == 0) return NM_OK;
+    const uintptr_t al16 = (uintptr_t)a.out | (uintptr_t)a.Tk | (uintptr_t)a.Tp | (uintptr_t)a.Tn | (uintptr_t)a.Z;
+    const uintptr_t al8 = (uintptr_t)a.x32 | (uintptr_t)a.e32 | (uintptr_t)a.Th | (uintptr_t)a.Tl;
+    if (a.b % 2 == 0 && (al16 & 15) == 0 && (al8 & 7) == 0 && (a.ldz % 2) == 0 && a.rows * a.b / 2 < (1ll << 30)) {
+        combine2_kernel<<<grid_for(a.rows * a.b / 2), kThreads, 0, s>>>(a);
+        count_launch();
+        NM_CUDA(cudaGetLastError());
+        return NM_OK;
+    }
     combine_kernel<<<grid_for(a.rows * a.b), kThreads, 0, s>>>(a);
     count_launch();
     NM_CUDA(cudaGetLastError());
