@@ -83,6 +83,27 @@ def parse():
     return ap.parse_args()
 
 
+def rank_slice(rank):
+    """The slice rank r solves: the units (slices) are sharded over ranks,
+    so the data path needs no collective."""
+    return SLICES_OMEGA[rank % len(SLICES_OMEGA)]
+
+
+def reduce_over_ranks(t_ms, pairs, world, device):
+    """Whole-job figures: the max over ranks of the timed region and the
+    sum over ranks of converged eigenpairs (one all-reduce each, after the
+    timed region)."""
+    if world <= 1:
+        return float(t_ms), int(pairs)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    pp = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    dist.all_reduce(pp, op=dist.ReduceOp.SUM)
+    return float(tt.item()), int(pp.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -258,7 +279,7 @@ def run_ours(args):
     P = nm.Problem(ctx, w.mesh, w.model)
     if args.chunk is not None:
         P.set_option("chunk", args.chunk)
-    lo, hi = SLICES_OMEGA[rank % len(SLICES_OMEGA)]
+    lo, hi = rank_slice(rank)
     P.set_interval(lo, hi)
     prec = {"f64": nm.NM_F64, "f32": nm.NM_F32, "mixed": nm.NM_MIXED}[args.prec]
     k_M = args.k_m or K_INNER[args.prec]
@@ -356,16 +377,7 @@ def run_ours(args):
     # steps (kind 2) in the mixed form, the mass-step launches (kind 0) else
     dl, dms = P.profile_read(2) if args.prec == "mixed" else (ml, mms)
     P.profile(False, reset=True)
-    # max over ranks of the timed region; eigenpairs summed over ranks
-    tot_pairs = good
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-        pp = torch.tensor([float(good)], device="cuda")
-        dist.all_reduce(pp, op=dist.ReduceOp.SUM)
-        tot_pairs = int(pp.item())
+    t_ms, tot_pairs = reduce_over_ranks(t_ms, good, world, "cuda")
     value = tot_pairs / (t_ms / 1e3)
 
     # end to end through the public API with host buffers, when the warm-up

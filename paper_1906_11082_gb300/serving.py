@@ -42,6 +42,7 @@ class Request:
     error: Optional[str] = None
     done: threading.Event = dataclasses.field(default_factory=threading.Event)
     slot: int = -1
+    run_bytes: int = 0
 
     @property
     def latency(self):
@@ -61,6 +62,7 @@ class _Slot(threading.Thread):
         self.index = index
         self.inbox = queue.Queue()
         self.problems = collections.OrderedDict()   # key -> Problem (LRU)
+        self.prob_bytes = {}                         # key -> bytes reserved for the resident problem
         self.ctx = None
         self.busy = False
 
@@ -86,6 +88,8 @@ class _Slot(threading.Thread):
             except Exception as ex:  # reported on the request, the slot keeps serving
                 req.error = repr(ex)
             req.t_done = time.perf_counter()
+            with self.server._lock:
+                self.server._running_bytes -= req.run_bytes
             self.busy = False
             req.done.set()
             self.server._wake.set()
@@ -94,19 +98,31 @@ class _Slot(threading.Thread):
         self.ctx.close()
 
     def evict_one(self):
+        """Free the least recently used resident problem of an idle slot."""
         if self.problems and not self.busy:
-            _, P = self.problems.popitem(last=False)
+            key, P = self.problems.popitem(last=False)
+            self.prob_bytes.pop(key, None)
             P.free()
             return True
         return False
 
 
 class SliceServer:
-    """FIFO admission by free slot and free HBM; concurrent execution."""
+    """FIFO admission by free slot and free HBM; concurrent execution.
+
+    Admission keeps a ledger of committed bytes (the estimates of running
+    solves and of resident problems), reserved when a request is admitted
+    and released when it completes or its problem is evicted: a slot
+    allocates only after admission, so the device's free memory alone would
+    let several requests in on the same bytes. A request is admitted when
+    it fits both the ledger (against the free memory at start, less the
+    reserve) and the device's current free memory."""
 
     def __init__(self, slots=2, device=0, reserve_bytes=2 << 30):
         self.device = device
         self.reserve = reserve_bytes
+        self._budget = _device_free_bytes(device) - reserve_bytes
+        self._running_bytes = 0
         self.pending = collections.deque()
         self.all = []
         self._lock = threading.Lock()
@@ -151,17 +167,31 @@ class SliceServer:
                         break
                     # prefer an idle slot that already holds the problem
                     slot = next((s for s in idle if req.key in s.problems), idle[0])
-                    need = self.estimate_bytes(req.n_dof_hint, req.opts, req.key in slot.problems)
-                    free = _device_free_bytes(self.device) - self.reserve
-                    while need > free and any(s.evict_one() for s in self.slots):
-                        free = _device_free_bytes(self.device) - self.reserve
-                    if need > free and any(s.busy for s in self.slots):
+                    resident = req.key in slot.problems
+                    run = self.estimate_bytes(req.n_dof_hint, req.opts, True)
+                    prob = 0 if resident else self.estimate_bytes(req.n_dof_hint, req.opts, False) - run
+                    need = run + prob
+                    while not self._fits(need) and any(s.evict_one() for s in self.slots if s is not slot or
+                                                      not resident):
+                        pass
+                    if not self._fits(need) and any(s.busy for s in self.slots):
                         break        # wait for memory to be released by a running request
                     self.pending.popleft()
+                    self._running_bytes += run
+                    req.run_bytes = run
+                    if prob:
+                        slot.prob_bytes[req.key] = prob
                     req.t_admit = time.perf_counter()
                     req.slot = slot.index
                     slot.busy = True
                     slot.inbox.put(req)
+
+    def _committed(self):
+        return self._running_bytes + sum(sum(s.prob_bytes.values()) for s in self.slots)
+
+    def _fits(self, need):
+        return (self._committed() + need <= self._budget and
+                need <= _device_free_bytes(self.device) - self.reserve)
 
     def drain(self, timeout=None):
         for r in list(self.all):
