@@ -3,8 +3,8 @@
 Test infrastructure (CPU oracle). The paper applies a polynomial filter
 with a Lanczos eigensolver to the pencil A u = w^2 M u and touches A, M
 and M^{-1} only through matrix-vector products (Sec. 6.2); it defers the
-filter and Lanczos details to its references. The readings used here
-(each listed in the design notes) are:
+filter and Lanczos details to its references. The readings used here,
+where the paper leaves the choice open, are:
 
 * Mass solve (M^{-1} "by matrix-vector multiplications"): k_M steps of
   Chebyshev semi-iteration preconditioned by D = diag(M) with fixed bounds
