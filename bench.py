@@ -1,14 +1,23 @@
-"""Benchmark: eigenpairs/s of one filtered-Lanczos spectrum slice on GB300.
+"""Benchmark: eigenpairs/s of a filtered-Lanczos spectrum-slice sweep on GB300.
 
 Workload (default): the three-layer planet (solid inner core, fluid outer
 core, solid mantle; seeded smooth profiles; reference gravity by direct
-summation; Cowling operator), P2 on ~2.6e5 tets (~1.1M dof), one
-low-frequency slice holding ~100 eigenpairs, block width 32. A step is one full slice solve: spectrum bounds, filtered block
-Lanczos, FP64 Rayleigh-Ritz and FP64 residuals (matrices resident,
-assembly excluded). The filter degree is 600, not the configured 100: on
-this mesh a degree-100 filter cannot keep the fluid core's essential
-spectrum near lambda = 0 out of the slice. value = eigenpairs with residual <= 1e-6 per second,
-summed over ranks (each rank solves its own slice; no collective).
+summation; Cowling operator), P2 on 263,760 tets (1.15M dof), slices of
+the low-frequency spectrum above the fluid band, block width 32, filter
+degree 600 (the configured degree 100 cannot keep the fluid core's
+essential spectrum near lambda = 0 out of the slice on this mesh).
+
+A step is ONE BLOCK STEP of a continuous sweep over adjacent slices
+(nm_lanczos_step): the degree-600 filter of the current 32-vector block
+(K_eff SpMMs and inner mass / pressure solves), two-pass CGS and
+Cholesky-QR in the M inner product, the projected matrix and, every
+second block, the convergence test; the step in which a slice converges
+also runs its FP64 Rayleigh-Ritz and residuals, and the next slice of the
+sweep begins in the following step. Matrices are resident; assembly and
+the spectrum bounds of P_M K_eff (shared by every slice of the problem)
+run before the timed region. The timed region starts on a fresh slice.
+value = eigenpairs with residual <= 1e-6 accepted during the timed steps,
+summed over ranks, divided by the max-over-ranks timed seconds.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|f64|f32]
        [--impl ours|reference]
@@ -16,7 +25,9 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|f64|f32
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -31,9 +42,10 @@ sys.path.insert(0, ROOT)
 METRIC = "eigenpairs/s per slice"
 UNIT = "eigenpairs/s"
 
-# Slice edges (angular frequency) of the layered-planet workload; rank r of
-# N solves slice r. The first slice holds ~100 eigenpairs above the fluid
-# band; later slices continue upward.
+# Adjacent slices (angular frequency) of the layered-planet workload. A
+# rank sweeps its own slices in order: r, r + N, r + 2N, ... (mod the list).
+# The first slice holds 90 eigenpairs above the fluid band; later slices
+# continue upward.
 SLICES_OMEGA = [(4.0, 6.5), (6.5, 7.6), (7.6, 8.4), (8.4, 9.0), (9.0, 9.6), (9.6, 10.1), (10.1, 10.5),
                 (10.5, 10.9)]
 H_MESH = 0.05
@@ -43,13 +55,9 @@ H_MESH = 0.05
 # below 0.7% of the slice's filter value.
 DEGREE_CONFIG = 100
 DEGREE = 600
-# The benchmark slice as the filtered Lanczos solves it: 90 eigenpairs with
-# residual <= 1e-6 after 18 blocks of 32 (measured); the reference arm
-# scales one timed CPU filter degree by degree x blocks of this slice.
-SLICE_PAIRS = 90
-SLICE_BLOCKS = 18
 BLOCK = 32
 K_INNER = {"f64": 38, "mixed": 20, "f32": 28}
+SEED = 11
 
 # Serving leg: layered planets of three sizes with the spectrum upper bound
 # the library's bounds estimate gives on each (lambda_max sets the filter
@@ -61,16 +69,29 @@ K_INNER = {"f64": 38, "mixed": 20, "f32": 28}
 SERVING_MESHES = [(0.25, 58954.0), (0.15, 45045.0), (0.1, 85700.0)]
 SERVING_SLICES = [(4.0, 5.5), (4.5, 6.0), (3.5, 5.0)]
 
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the
+# float mass-step kernel (kron_v4_kernel<3, 1, 32>) on this workload (same
+# matrices, b = 32), captured with `ncu --set full --clock-control none -k
+# regex:kron_v4_kernel -s 4 -c 2` around `bench.py --profile-case`, and the
+# SHA-256 of kernels.cu when it was taken: once the kernel source changes
+# the figure no longer describes it and the bench reports traffic null.
+TRAFFIC_CAPTURE = {"kernel": "kron_v4_kernel<3, 1, 32>", "bytes": 543_801_344 + 123_877_376,
+                   "kernels_cu_sha256": None}
+
+# FP64 peak of GB300 (NVIDIA's published B300 figure, 1.25 TFLOP/s; equal to
+# 152 SMs x ~2.05 GHz x 2 FP64 FMA per SM per clock x 2 flop).
+FP64_PEAK_TFLOPS = 1.25
+
 
 def serving_degree(lam_max, lo, hi):
     return int(np.ceil(1.7 * np.pi * np.sqrt(lam_max) / (2.0 * (hi - lo))))
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--prec", choices=("mixed", "f64", "f32"), default="mixed")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--h", type=float, default=H_MESH)
@@ -85,13 +106,21 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--no-f64-leg", action="store_true")
+    ap.add_argument("--f64-steps", type=int, default=2)
+    ap.add_argument("--cpu-workers", type=int, default=0, help="0: all host cores (up to the block width)")
+    return ap.parse_args(argv)
 
 
 def rank_slice(rank):
-    """The slice rank r solves: the units (slices) are sharded over ranks,
-    so the data path needs no collective."""
+    """The first slice rank r solves: the units (slices) are sharded over
+    ranks, so the data path needs no collective."""
     return SLICES_OMEGA[rank % len(SLICES_OMEGA)]
+
+
+def rank_sweep(rank, world, count):
+    """The first `count` slices of rank r's sweep: r, r + N, r + 2N, ..."""
+    return [SLICES_OMEGA[(rank + i * world) % len(SLICES_OMEGA)] for i in range(count)]
 
 
 def reduce_over_ranks(t_ms, pairs, world, device):
@@ -126,6 +155,7 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.p = None
+        self.out = ""
 
     def __enter__(self):
         try:
@@ -175,15 +205,9 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the float
-# mass-step kernel (kron_v4_kernel<3, 1, 32>) on this workload, from the ncu
-# capture summarised in profiles/kron_v4_mass_step_planet_h0.05_b32.md
-# (same matrices and block width as the timed launches).
-V4_TRAFFIC_BYTES = 543_801_344 + 123_877_376
-
-# FP64 peak of GB300 (NVIDIA's published B300 figure, 1.25 TFLOP/s; equal to
-# 152 SMs x ~2.05 GHz x 2 FP64 FMA per SM per clock x 2 flop).
-FP64_PEAK_TFLOPS = 1.25
+def kernels_sha256():
+    with open(os.path.join(ROOT, "paper_1906_11082_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
 
 
 def mass_step_bytes(info, b, s):
@@ -202,14 +226,20 @@ def workload(h):
     return config_layered(h=h)
 
 
-def cpu_sample(w, prec, b, k_M, warm=0, steps=1):
-    """The oracle as it stands, on a bounded sample: one filter degree
-    (K_eff + mass solve) for b vectors on the octant x, y, z > 0 of the mesh.
-    The mixed form's oracle counterpart applies the refined solves in FP64.
-    Returns (seconds per step, stored blocks of the sample, tets, dof)."""
+# ------------------------------------------------------------------ CPU legs
+# The oracle as it stands, on a bounded sample: one filter degree (K_eff +
+# inner mass solve) for the 32 vectors of a block on the octant x, y, z > 0
+# of the mesh, scaled to the full mesh by stored blocks. All cores: the 32
+# columns are split over worker processes (the operator acts on each column
+# on its own), each worker assembling the octant itself; one core: one
+# worker with all 32 columns. Workers are started with `spawn` and run with
+# one BLAS / OpenMP thread each, so `cores` is the number of processes.
+
+def _octant_operator(h, prec, k_M):
     import copy
     from synth.mesh import Mesh
     from oracle import fem, filtlan
+    w = workload(h)
     m = w.mesh
     c = m.xyz[m.tet].mean(axis=1)
     sel = np.nonzero((c > 0).all(axis=1))[0]
@@ -219,54 +249,202 @@ def cpu_sample(w, prec, b, k_M, warm=0, steps=1):
         setattr(mdl, k, getattr(w.model, k)[sel])
     S = fem.assemble(sub, mdl)
     op = filtlan.Operator(S, k_M=k_M, k_P=k_M, refine=(prec == "mixed"))
-    Y = np.random.default_rng(0).standard_normal((S.n, b))
-    if prec == "f32":
-        Y = Y.astype(np.float32)
-    times = []
-    for i in range(warm + steps):
-        t = time.perf_counter()
-        op.B(Y)
-        if i >= warm:
-            times.append(time.perf_counter() - t)
-    blocks_sub = S.A_G.nnz / 9
-    return float(np.mean(times)), blocks_sub, len(sel), S.n
+    return op, S, len(sel)
+
+
+def _cpu_worker(conn, h, prec, k_M, c0, c1):
+    try:
+        op, S, nt = _octant_operator(h, prec, k_M)
+        Y = np.ascontiguousarray(np.random.default_rng(0).standard_normal((S.n, BLOCK))[:, c0:c1])
+        if prec == "f32":
+            Y = Y.astype(np.float32)
+        conn.send(("ready", S.n, nt, S.A_G.nnz / 9))
+        while True:
+            msg = conn.recv()
+            if msg == "stop":
+                break
+            t0 = time.time()
+            op.B(Y)
+            conn.send((t0, time.time()))
+    except Exception as ex:  # reported to the parent, which raises
+        conn.send(("error", repr(ex)))
+    finally:
+        conn.close()
+
+
+class CpuPool:
+    """`workers` spawned oracle processes holding the octant operator, each
+    with its share of the block's columns."""
+
+    def __init__(self, h, prec, k_M, workers):
+        ctx = mp.get_context("spawn")
+        env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in env_keep:
+            os.environ[k] = "1"
+        self.procs, self.conns = [], []
+        try:
+            cuts = np.linspace(0, BLOCK, workers + 1).round().astype(int)
+            for i in range(workers):
+                a, b = ctx.Pipe()
+                p = ctx.Process(target=_cpu_worker, args=(b, h, prec, k_M, int(cuts[i]), int(cuts[i + 1])),
+                                daemon=True)
+                p.start()
+                self.procs.append(p)
+                self.conns.append(a)
+        finally:
+            for k, v in env_keep.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.info = None
+        for c in self.conns:
+            r = c.recv()
+            if r[0] != "ready":
+                self.close()
+                raise RuntimeError(f"oracle worker failed: {r[1]}")
+            self.info = r[1:]
+        self.workers = workers
+
+    def degree(self):
+        """Wall seconds of one filter degree with every worker on its columns."""
+        for c in self.conns:
+            c.send("go")
+        spans = [c.recv() for c in self.conns]
+        for s in spans:
+            if s[0] == "error":
+                raise RuntimeError(f"oracle worker failed: {s[1]}")
+        return max(s[1] for s in spans) - min(s[0] for s in spans)
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send("stop")
+            except (OSError, BrokenPipeError):
+                pass
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def cpu_workers(requested):
+    n = os.cpu_count() or 1
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        pass
+    return max(1, min(requested or n, BLOCK))
+
+
+def _graph_blocks(mesh):
+    from oracle import fem
+    dm = fem.dof_map(mesh.tet, mesh.region, mesh.nv)
+    un = dm.elem_unodes(np.asarray(mesh.region))
+    a = np.repeat(un, 10, axis=1).ravel()
+    b = np.tile(un, (1, 10)).ravel()
+    key = np.unique(a.astype(np.int64) * dm.Nu + b)
+    return len(key)
+
+
+def cpu_baseline(h, prec, k_M, pairs, blocks, degree, blocks_full, workers, reps=2):
+    """The oracle's eigenpairs/s on all cores and on one core, scaled from
+    one timed filter degree on the octant sample to the benchmark slice."""
+    out = {}
+    for label, nw in (("all", workers), ("one", 1)):
+        pool = CpuPool(h, prec, k_M, nw)
+        try:
+            pool.degree()   # warm
+            t = min(pool.degree() for _ in range(reps))
+        finally:
+            pool.close()
+        n_sub, nt_sub, blocks_sub = pool.info
+        t_deg = t * blocks_full / blocks_sub
+        out[label] = {"value": pairs / (t_deg * degree * blocks), "cores": nw, "sample_degree_s": t,
+                      "full_degree_s": t_deg, "sample_tets": int(nt_sub), "sample_dof": int(n_sub)}
+    a, o = out["all"], out["one"]
+    sample = (f"one filter degree (K_eff + {k_M}-step inner solves, {'refined ' if prec == 'mixed' else ''}"
+              f"FP64) on {BLOCK} vectors over the octant x,y,z>0 ({a['sample_tets']} tets, {a['sample_dof']} "
+              f"dof; {a['sample_degree_s']:.2f} s on {a['cores']} processes, {o['sample_degree_s']:.2f} s on "
+              f"one), scaled by stored blocks to the full mesh and by degree {degree} x {blocks} Lanczos "
+              f"blocks to the {pairs}-pair slice")
+    return {"value": a["value"], "unit": UNIT, "cores": a["cores"], "kind": "oracle", "sample": sample,
+            "one_core": {"value": o["value"], "unit": UNIT, "cores": 1},
+            "nproc": os.cpu_count()}
+
+
+# Pairs and blocks of the benchmark slice (4.0, 6.5) as the mixed-form
+# sweep converges it (90 eigenpairs with residual <= 1e-6 in 18 blocks of
+# 32); the reference arm scales its timed oracle degree by these.
+SLICE_PAIRS = 90
+SLICE_BLOCKS = 18
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
         return
-    w = workload(args.h)
     k_M = args.k_m or K_INNER[args.prec]
-    t_step, blocks_sub, nt_sub, n_sub = cpu_sample(w, args.prec, BLOCK, k_M, warm=args.warmup, steps=args.steps)
-    # full-mesh scale from the stored-block count of the full graph
-    from oracle import fem
-    dm = fem.dof_map(w.mesh.tet, w.mesh.region, w.mesh.nv)
-    blocks_full = _graph_blocks(w.mesh, dm)
+    w = workload(args.h)
+    blocks_full = _graph_blocks(w.mesh)
+    workers = cpu_workers(args.cpu_workers)
+    pool = CpuPool(args.h, args.prec, k_M, workers)
+    try:
+        for _ in range(args.warmup):
+            pool.degree()
+        times = [pool.degree() for _ in range(args.steps)]
+    finally:
+        pool.close()
+    n_sub, nt_sub, blocks_sub = pool.info
+    t_step = float(np.mean(times))
     t_deg = t_step * blocks_full / blocks_sub
-    nev, nblocks = SLICE_PAIRS, SLICE_BLOCKS
-    value = nev / (t_deg * args.degree * nblocks)
-    cores = 1
+    value = SLICE_PAIRS / (t_deg * args.degree * SLICE_BLOCKS)
+    sample = (f"each step: one filter degree (K_eff + {k_M}-step inner solves) on {BLOCK} vectors over the "
+              f"octant x,y,z>0 ({nt_sub} tets, {n_sub} dof) on {workers} oracle processes; value scales the "
+              f"mean step by stored blocks to the full mesh and by degree {args.degree} x {SLICE_BLOCKS} blocks "
+              f"to the {SLICE_PAIRS}-pair benchmark slice")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "tets": int(w.mesh.nt), "degree": args.degree, "block": BLOCK},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"one filter degree (K_eff + {k_M}-step mass solve) on {BLOCK} vectors "
-                                       f"over the octant x,y,z>0 ({nt_sub} tets, {n_sub} dof), scaled by "
-                                       f"stored blocks to the full mesh and by degree {args.degree} x {nblocks} "
-                                       f"blocks to the {nev}-pair benchmark slice (the same algorithm "
-                                       f"converges it in {nblocks} blocks)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample,
+                             "nproc": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-def _graph_blocks(mesh, dm):
-    un = dm.elem_unodes(np.asarray(mesh.region))
-    a = np.repeat(un, 10, axis=1).ravel()
-    b = np.tile(un, (1, 10)).ravel()
-    key = np.unique(a.astype(np.int64) * dm.Nu + b)
-    return len(key)
+# ------------------------------------------------------------------ GPU arm
+class Sweep:
+    """A continuous sweep over a rank's slices, one block step per call."""
+
+    def __init__(self, P, slices, opts):
+        self.P = P
+        self.slices = slices
+        self.opts = opts
+        self.i = 0
+        self.run = None
+        self.done = []   # (slice, pairs passing 1e-6, blocks, max resid)
+
+    def _begin(self):
+        self.run = self.P.lanczos_begin([self.slices[self.i % len(self.slices)]], **self.opts)
+
+    def step(self):
+        if self.run is None:
+            self._begin()
+        if self.run.step() == 0:
+            info = self.run.info(0)
+            res = self.run.finish(allow_unconverged=True)[0]
+            good = int(np.sum(res.resid <= 1e-6))
+            self.done.append((self.slices[self.i % len(self.slices)], good, int(info["blocks"]),
+                              float(res.resid.max()) if len(res.lam) else 0.0))
+            res.free()
+            self.run = None
+            self.i += 1
+            return good
+        return 0
+
+    def close(self):
+        if self.run is not None:
+            self.run.free()
+            self.run = None
 
 
 def run_ours(args):
@@ -282,15 +460,18 @@ def run_ours(args):
 
     w = workload(args.h)
     ctx = nm.Context(local)
+    torch.cuda.synchronize()
+    t_asm = time.perf_counter()
     P = nm.Problem(ctx, w.mesh, w.model)
+    t_asm = time.perf_counter() - t_asm
     if args.chunk is not None:
         P.set_option("chunk", args.chunk)
-    lo, hi = rank_slice(rank)
-    P.set_interval(lo, hi)
     prec = {"f64": nm.NM_F64, "f32": nm.NM_F32, "mixed": nm.NM_MIXED}[args.prec]
     k_M = args.k_m or K_INNER[args.prec]
     opts = dict(block=BLOCK, degree=args.degree, k_M=k_M, k_P=k_M, max_blocks=args.max_blocks, check_every=2,
-                prec=prec, seed=11 + rank, allow_unconverged=True)
+                prec=prec, seed=SEED + rank)
+    lo, hi = rank_slice(rank)
+    P.set_interval(lo, hi)
     if args.profile_case:
         lo_b, hi_b = P.spectrum_bounds(steps=40, k_M=k_M)
         g, c, e = nm.filter_design(lo_b, hi_b, lo * lo, hi * hi, 10)
@@ -298,15 +479,10 @@ def run_ours(args):
         Z = torch.empty_like(Y)
         P.filter_apply(g, c, e, k_M, Y, Z, prec=nm.NM_MIXED)
         torch.cuda.synchronize()
-        torch.cuda.nvtx.range_push("filter")
         P.filter_apply(g, c, e, k_M, Y, Z, prec=nm.NM_MIXED)
         torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
         print(json.dumps({"profile_case": "mixed filter, degree 10, b = 32", "n": P.n}))
         return
-
-    def step():
-        return P.lanczos_slice(**opts)
 
     def barrier():
         if world > 1:
@@ -314,104 +490,101 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def e2e_steps(count):
-        """`count` steps end to end through the public API: every step copies
-        its start block from pinned host memory to the device, solves the
-        slice, and copies eigenvectors and eigenvalues back to the host."""
-        n = P.n
-        host_start = torch.randn((n, BLOCK), dtype=torch.float64).pin_memory()
-        dev_start = torch.empty((n, BLOCK), dtype=torch.float64, device="cuda")
-        host_out = None
-        barrier()
-        t0 = time.perf_counter()
-        pairs = h2d = d2h = 0
-        for _ in range(count):
-            dev_start.copy_(host_start, non_blocking=True)
-            torch.cuda.synchronize()
-            r = P.lanczos_slice(**dict(opts, start=dev_start))
-            X = r.vectors()
-            if host_out is None or host_out.shape != X.shape:
-                host_out = torch.empty(X.shape, dtype=X.dtype).pin_memory()
-            host_out.copy_(X)
-            lam = r.lam.copy()
-            pairs += int(np.sum(r.resid <= 1e-6))
-            h2d += host_start.numel() * 8
-            d2h += X.numel() * 8 + 2 * lam.size * 8
-            r.free()
-            del X
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        return {"value": pairs / dt, "unit": UNIT, "h2d_bytes_per_step": h2d // count,
-                "d2h_bytes_per_step": d2h // count, "steps": count}
-
-    # Warm-up: the first step plain; with W >= 2 the remaining W - 1 warm-up
-    # steps are the end-to-end measurement (warm, untimed for `value`).
-    e2e = None
-    n_e2e_warm = args.warmup - 1 if (not args.no_e2e and args.warmup >= 2) else 0
-    for _ in range(args.warmup - n_e2e_warm):
-        r = step()
-        r.free()
-    if n_e2e_warm:
-        e2e = e2e_steps(n_e2e_warm)
-        e2e["note"] = "measured on warm-up steps 2..W"
+    # Warm-up: W block steps of the rank's first slice (this also computes
+    # the spectrum bounds the problem keeps for every later slice); the run
+    # is then dropped, so the timed sweep starts on a fresh slice.
+    warm = P.lanczos_begin([rank_slice(rank)], **opts)
+    for _ in range(args.warmup):
+        warm.step()
+    warm.free()
 
     P.profile(True, reset=True)
-    launches0 = nm.kernel_launches()
+    sweep = Sweep(P, rank_sweep(rank, world, len(SLICES_OMEGA)), opts)
     lat = []
-    results = []
+    pairs = 0
     barrier()
+    launches0 = nm.kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         ev0.record()
         for _ in range(args.steps):
             t = time.perf_counter()
-            r = step()
+            pairs += sweep.step()
             lat.append(time.perf_counter() - t)
-            results.append((int(np.sum(r.resid <= 1e-6)), float(r.resid.max()) if len(r.lam) else 0.0,
-                            dict(r.info, found=len(r.lam))))
-            r.free()
         ev1.record()
         barrier()
     launches = nm.kernel_launches() - launches0
     t_ms = ev0.elapsed_time(ev1)
-    good = sum(k for k, _, _ in results)
-    k_last, res_last, info_last = results[-1]
+    partial = sweep.run.info(0) if sweep.run is not None else None
+    sweep.close()
     ml, mms = P.profile_read(0)
     kl, kms = P.profile_read(1)
     # the dominant kernel's own launches: the float M_rho semi-iteration
     # steps (kind 2) in the mixed form, the mass-step launches (kind 0) else
     dl, dms = P.profile_read(2) if args.prec == "mixed" else (ml, mms)
     P.profile(False, reset=True)
-    t_ms, tot_pairs = reduce_over_ranks(t_ms, good, world, "cuda")
+    t_ms, tot_pairs = reduce_over_ranks(t_ms, pairs, world, "cuda")
     value = tot_pairs / (t_ms / 1e3)
-
-    # end to end through the public API with host buffers, when the warm-up
-    # was too short to carry it
-    if e2e is None and not args.no_e2e:
-        e2e = e2e_steps(args.steps)
-
+    done = sweep.done
     if rank != 0:
         return
     info = P.info
-    # per-degree cost of the plain FP64 filter (same slice, k = 38) for the
-    # FP64-form comparison; measured outside the timed region
-    lo_b, hi_b = P.spectrum_bounds(steps=40, k_M=K_INNER["f64"])
-    g4, c4, e4 = nm.filter_design(lo_b, hi_b, lo * lo, hi * hi, 4)
-    Yb = torch.randn((P.n, BLOCK), dtype=torch.float64, device="cuda")
-    Zb = torch.empty_like(Yb)
-    per_deg = {}
-    for name, pr, kk in (("f64", nm.NM_F64, K_INNER["f64"]), ("mixed", nm.NM_MIXED, K_INNER["mixed"])):
-        P.filter_apply(g4, c4, e4, kk, Yb, Zb, prec=pr)
+    first = done[0] if done else None
+    slice_pairs = first[1] if first else 0
+    slice_blocks = first[2] if first else 0
+
+    # end to end through the public API: one full slice solve of the first
+    # slice (nm_lanczos_slice) with its start block copied from pinned host
+    # memory and eigenvalues, residuals and eigenvectors copied back
+    e2e = None
+    if not args.no_e2e:
+        host_start = torch.from_numpy(np.random.default_rng(SEED).standard_normal((P.n, BLOCK))).pin_memory()
+        dev_start = torch.empty((P.n, BLOCK), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dev_start.copy_(host_start, non_blocking=True)
+        torch.cuda.synchronize()
+        r = P.lanczos_slice(**dict(opts, start=dev_start), allow_unconverged=True)
+        X = r.vectors()
+        host_out = torch.empty(X.shape, dtype=X.dtype).pin_memory()
+        host_out.copy_(X)
+        torch.cuda.synchronize()
+        lam = r.lam.copy()
+        e2e_pairs = int(np.sum(r.resid <= 1e-6))
+        dt = time.perf_counter() - t0
+        e2e = {"value": e2e_pairs / dt, "unit": UNIT, "h2d_bytes_per_step": int(host_start.numel() * 8),
+               "d2h_bytes_per_step": int(X.numel() * 8 + 2 * lam.size * 8), "steps": 1,
+               "step": "one nm_lanczos_slice call on the first slice (host start block in, eigenpairs out)",
+               "eigenpairs": e2e_pairs, "seconds": dt}
+        r.free()
+        del X, dev_start
+
+    # the plain FP64 form on the same slice: block steps of its own run
+    # (FP64 filter, k = 38 inner steps), timed with CUDA events, after one
+    # untimed step (its spectrum bounds and start)
+    f64 = None
+    if not args.no_f64_leg and args.prec != "f64" and args.f64_steps > 0:
+        k64 = K_INNER["f64"]
+        run = P.lanczos_begin([rank_slice(rank)], **dict(opts, prec=nm.NM_F64, k_M=k64, k_P=k64))
+        run.step()
         torch.cuda.synchronize()
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record()
-        P.filter_apply(g4, c4, e4, kk, Yb, Zb, prec=pr)
+        for _ in range(args.f64_steps):
+            run.step()
         a1.record()
         torch.cuda.synchronize()
-        per_deg[name] = a0.elapsed_time(a1) / 4.0
-    blocks_used = max(int(info_last["blocks"]), 1)
+        run.free()
+        ms64 = a0.elapsed_time(a1) / args.f64_steps
+        ms_mixed = t_ms / args.steps
+        f64 = {"ms_per_block_step": ms64, "steps_timed": args.f64_steps, "k_inner": k64,
+               "mixed_ms_per_block_step": ms_mixed,
+               "speedup_mixed_over_f64": ms64 / ms_mixed}
+        if slice_blocks:
+            f64["eigenpairs_per_s_at_same_blocks"] = slice_pairs / (ms64 / 1e3 * slice_blocks)
+
     s = 8 if args.prec == "f64" else 4   # the dominant mass-step kernel's value size
     peak_hbm, peak_src = peaks()
     # average duration of one launch of the dominant kernel, from CUDA
@@ -422,15 +595,17 @@ def run_ours(args):
     mflops = mass_step_flops(info, BLOCK)
     gbs = mbytes / avg_launch_s / 1e9 if dl else None
     tfl = mflops / avg_launch_s / 1e12 if dl else None
+    traffic = None
+    if (s == 4 and args.h == H_MESH and TRAFFIC_CAPTURE["kernels_cu_sha256"] == kernels_sha256()):
+        traffic = TRAFFIC_CAPTURE["bytes"]
     if args.prec == "f64" and tfl is not None and tfl / FP64_PEAK_TFLOPS > gbs / peak_hbm:
         roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "kron_warp_kernel<double, 3, 1, 1>",
                 "peak_source": "GB300 FP64 nominal (152 SM x 2 FMA/clk x 2.05 GHz)"}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": peak_hbm, "unit": "GB/s",
-                "frac": (gbs / peak_hbm) if gbs else None,
-                "traffic": V4_TRAFFIC_BYTES if (s == 4 and args.h == H_MESH) else None,
-                "kernel": "kron_warp_kernel<double, 3, 1, 1>" if s == 8 else "kron_v4_kernel<3, 1, 32>",
+                "frac": (gbs / peak_hbm) if gbs else None, "traffic": traffic,
+                "kernel": "kron_warp_kernel<double, 3, 1, 1>" if s == 8 else TRAFFIC_CAPTURE["kernel"],
                 "peak_source": f"{peak_src} copy bandwidth"}
     roof["bytes_per_launch"] = mbytes
     roof["flops_per_launch"] = mflops
@@ -443,20 +618,23 @@ def run_ours(args):
             "dtype": {"mixed": "f64+f32", "f64": "f64", "f32": "f32+f64"}[args.prec], "data": "synthetic",
             "config": {"workload": w.name, "tets": int(w.mesh.nt), "dof": int(info["n"]),
                        "pressure_dof": int(info["Np"]), "degree": args.degree, "degree_config": DEGREE_CONFIG,
-                       "block": BLOCK, "k_inner": k_M,
-                       "slice_omega": [lo, hi], "eigenpairs": int(k_last), "max_resid": res_last,
-                       "lanczos_blocks": int(info_last["blocks"]), "filter_prec": args.prec,
+                       "block": BLOCK, "k_inner": k_M, "filter_prec": args.prec,
+                       "step": "one block step of a slice sweep (filter, CGS2, Cholesky-QR; Rayleigh-Ritz "
+                               "in the step a slice converges)",
+                       "sweep_omega": rank_sweep(rank, world, max(len(done) + 1, 1)),
                        "parallelism": f"slices x{world}",
-                       "l2": "inputs larger than L2 (A_G %.2f GB resident)" % (info["nnz_u"] * 76 / 1e9)},
+                       "l2": "inputs larger than L2 (A_G %.2f GB resident)" % (info["nnz_u"] * 76 / 1e9),
+                       "untimed_prologue": "assembly (%.1f s) and the spectrum bounds shared by every slice"
+                                           % t_asm},
+            "slices_completed": [{"omega": list(sl), "eigenpairs": g, "blocks": bk, "max_resid": mr}
+                                 for sl, g, bk, mr in done],
+            "slice_in_progress": partial,
             "gpu_launches": int(launches),
             "roofline": roof,
-            "filter_apply": {"mass_steps_ms": mms, "k_apply_ms": kms, "share_of_step":
-                             filt_ms / max(t_ms, 1e-9)},
-            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3)},
-            "forms_ms_per_degree_b32": per_deg,
-            "f64_form_estimate": {"value": k_last / (per_deg["f64"] / 1e3 * args.degree * blocks_used),
-                                  "unit": UNIT, "basis": "plain FP64 filter ms/degree x degree x the Lanczos "
-                                                         "blocks of this run (filter time only)"},
+            "filter_apply": {"mass_steps_ms": mms, "k_apply_ms": kms, "share_of_step": filt_ms / max(t_ms, 1e-9)},
+            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                           "of": "block steps"},
+            "f64_form": f64,
             "e2e": e2e, "clocks": clk.summary()}
     if not args.no_serving and world == 1:
         P.free()
@@ -465,15 +643,12 @@ def run_ours(args):
         except Exception as ex:  # the serving leg must not cost the slice measurement
             line["serving"] = {"error": repr(ex)}
     if not args.no_cpu_baseline:
-        t_step, blocks_sub, nt_sub, n_sub = cpu_sample(w, args.prec, BLOCK, k_M)
-        blocks_full = info["nnz_u"]
-        t_deg = t_step * blocks_full / blocks_sub
-        cpu_val = max(k_last, 1) / (t_deg * args.degree * max(int(info_last["blocks"]), 1))
-        line["cpu_baseline"] = {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"one filter degree (K_eff + {k_M}-step mass solve) on {BLOCK} vectors "
-                                          f"over the octant x,y,z>0 ({nt_sub} tets, {n_sub} dof, "
-                                          f"{t_step:.1f} s), scaled by stored blocks to the full mesh and by "
-                                          f"degree x Lanczos blocks of the GPU run"}
+        try:
+            line["cpu_baseline"] = cpu_baseline(args.h, args.prec, k_M, max(slice_pairs, 1),
+                                                max(slice_blocks, 1), args.degree, int(info["nnz_u"]),
+                                                cpu_workers(args.cpu_workers))
+        except Exception as ex:
+            line["cpu_baseline"] = {"error": repr(ex)}
     print(json.dumps(line))
 
 
@@ -497,7 +672,6 @@ def run_serving(args, device):
         return build
 
     srv = SliceServer(slots=3, device=device)
-    reqs = []
     sizes = {}
     for i in range(args.serving_requests):
         h, lam_max = SERVING_MESHES[int(rng.integers(len(SERVING_MESHES)))]
@@ -507,8 +681,7 @@ def run_serving(args, device):
         if h not in sizes:
             m, _ = builder(h)()
             sizes[h] = int(m.nt)
-        reqs.append(srv.submit(Request(key=f"planet-h{h}", build=builder(h), interval=iv, opts=opts),
-                               5 * sizes[h]))
+        srv.submit(Request(key=f"planet-h{h}", build=builder(h), interval=iv, opts=opts), 5 * sizes[h])
         time.sleep(float(rng.exponential(1.0)))
     srv.drain(timeout=1800)
     st = srv.stats()

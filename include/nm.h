@@ -70,6 +70,7 @@ typedef enum { NM_RITZ_PENCIL = 0, NM_RITZ_ROTATING = 1 } nm_ritz_mode;
 typedef struct nm_ctx nm_ctx;
 typedef struct nm_problem nm_problem;
 typedef struct nm_result nm_result;
+typedef struct nm_lanczos nm_lanczos;
 
 /* Mesh (host memory, read during nm_assemble only).
  * xyz[3*nv] vertex coordinates; tet[4*nt] vertex ids (0-based, any
@@ -315,6 +316,57 @@ int nm_lanczos_slice(nm_problem* prob, const nm_slice_opts* opts, nm_result** ou
  * NM_ENOTCONV if any slice stops at max_blocks (every result is returned). */
 int nm_lanczos_multi(nm_problem* prob, const nm_slice_opts* opts, int nslices, const double* lo, const double* hi,
                      nm_unit unit, nm_result** out);
+
+/* ---- resumable block Lanczos ----------------------------------------------
+ * The filtered block Lanczos of nm_lanczos_slice / nm_lanczos_multi
+ * (Sec. 6.2) split into its block steps, so that a caller can interleave
+ * slices, bound the work per call, or stop early:
+ *
+ *   nm_lanczos_begin  spectrum bounds of P_M K_eff (reused when the problem
+ *                     already holds bounds for the same bounds_steps, k_M
+ *                     and seed + 1; any nm_set_option clears them), the
+ *                     filter of each slice, the start block (opts->start,
+ *                     read during this call only, else Philox from seed)
+ *                     and its Cholesky-QR in the M inner product.
+ *                     nslices = 0 takes the one interval of nm_set_interval
+ *                     (lo, hi, unit ignored); else as nm_lanczos_multi.
+ *   nm_lanczos_step   one block step of every active slice: filter the
+ *                     current blocks (one recurrence over the concatenated
+ *                     blocks), two-pass CGS and Cholesky-QR of each new
+ *                     block, the projected block-tridiagonal matrix; every
+ *                     check_every blocks (and at max_blocks) the Ritz
+ *                     convergence test and, when every wanted Ritz value of
+ *                     p(B) has converged, the FP64 Rayleigh-Ritz of the
+ *                     pencil; a slice whose Ritz pairs all pass tol stops.
+ *                     *active = slices still running (0: call finish).
+ *   nm_lanczos_get_info progress of slice i (host copy, no synchronisation).
+ *   nm_lanczos_finish the results of every slice (out: caller array of
+ *                     nslices pointers; a Rayleigh-Ritz on the current basis
+ *                     of a slice that has none yet). NM_ENOTCONV if a slice
+ *                     did not pass tol; the results are returned all the
+ *                     same and belong to the caller (nm_result_free).
+ *   nm_lanczos_free   releases the run (its bases); call after finish, or
+ *                     instead of it to abandon the run.
+ *
+ * Running begin, step until *active == 0, finish computes exactly what
+ * nm_lanczos_multi computes. The run borrows the problem: free it before
+ * the problem, and use one run of a problem at a time from one thread. */
+typedef struct {
+    int32_t blocks;          /* block steps taken by this slice             */
+    int32_t m;               /* basis columns                               */
+    int32_t active;          /* 1 while the slice takes further steps       */
+    int32_t converged;       /* 1 once its Rayleigh-Ritz pairs pass tol      */
+    int32_t wanted;          /* Ritz values of p(B) above the threshold      */
+    int32_t ritz_converged;  /* ... whose residual estimate passed           */
+    double seconds_filter;   /* filter time of the run so far               */
+} nm_lanczos_info;
+
+int nm_lanczos_begin(nm_problem* prob, const nm_slice_opts* opts, int nslices, const double* lo, const double* hi,
+                     nm_unit unit, nm_lanczos** out);
+int nm_lanczos_step(nm_lanczos* run, int* active);
+int nm_lanczos_get_info(const nm_lanczos* run, int slice, nm_lanczos_info* info);
+int nm_lanczos_finish(nm_lanczos* run, nm_result** out);
+int nm_lanczos_free(nm_lanczos* run);
 
 /* Rayleigh-Ritz on a caller basis V (device, n x m, row-major, ld ldv,
  * FP64). NM_RITZ_PENCIL: Ritz pairs of (K_eff, M) on span V inside the

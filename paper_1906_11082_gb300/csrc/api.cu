@@ -36,6 +36,13 @@ int spectrum_bounds(nm_problem* P, int steps, int k_M, uint64_t seed, double* la
 int lanczos_slice(nm_problem* P, const nm_slice_opts* o, nm_result** out);
 int lanczos_multi(nm_problem* P, const nm_slice_opts* o, int S, const double* lam_lo_in, const double* lam_hi_in,
                   nm_result** out);
+int lanczos_begin(nm_problem* P, const nm_slice_opts* o, int S, const double* lam_lo_in, const double* lam_hi_in,
+                  nm_lanczos** out);
+int lanczos_step(nm_lanczos* L, int* active_out);
+int lanczos_finish(nm_lanczos* L, nm_result** out);
+int lanczos_state(const nm_lanczos* L, int slice, nm_lanczos_info* out);
+void lanczos_free(nm_lanczos* L);
+nm_ctx* lanczos_ctx(const nm_lanczos* L);
 int ritz(nm_problem* P, nm_ritz_mode mode, const double* V, int64_t ldv, int m, const double* lam_e,
          nm_result** out);
 int profile_read(nm_problem* P, int kind, int64_t* launches, double* ms);
@@ -209,6 +216,7 @@ int nm_problem_export(const nm_problem* P, int which, int64_t* nrows, int64_t* n
 int nm_set_option(nm_problem* P, const char* key, int64_t value) {
     if (!P || !key) return fail(NM_EINVAL, "null argument");
     CtxScope sc(P->ctx);
+    P->have_bounds = 0;   // the stored spectrum bounds are recomputed under the new option
     if (std::string(key) == "tile_rows") {
         cudaStreamSynchronize(P->ctx->stream);
         return set_tile_rows(P, value);
@@ -395,13 +403,12 @@ int nm_lanczos_slice(nm_problem* P, const nm_slice_opts* opts, nm_result** out) 
     return lanczos_slice(P, opts, out);
 }
 
-int nm_lanczos_multi(nm_problem* P, const nm_slice_opts* opts, int nslices, const double* lo, const double* hi,
-                     nm_unit unit, nm_result** out) {
-    if (!P || !opts || !out || !lo || !hi || nslices < 1) return fail(NM_EINVAL, "bad argument");
-    CtxScope sc(P->ctx);
-    std::vector<double> l(nslices), u(nslices);
+// Interval of slice i in lambda (unit conversion as in nm_set_interval).
+static int slice_lambda(int nslices, const double* lo, const double* hi, nm_unit unit, std::vector<double>& l,
+                        std::vector<double>& u) {
+    l.resize(nslices);
+    u.resize(nslices);
     for (int i = 0; i < nslices; ++i) {
-        out[i] = nullptr;
         if (!(hi[i] > lo[i]) || !std::isfinite(lo[i]) || !std::isfinite(hi[i]))
             return fail(NM_EINVAL, "each slice needs finite lo < hi");
         if (unit == NM_UNIT_OMEGA) {
@@ -415,7 +422,58 @@ int nm_lanczos_multi(nm_problem* P, const nm_slice_opts* opts, int nslices, cons
             return fail(NM_EINVAL, "unknown unit");
         }
     }
+    return NM_OK;
+}
+
+int nm_lanczos_multi(nm_problem* P, const nm_slice_opts* opts, int nslices, const double* lo, const double* hi,
+                     nm_unit unit, nm_result** out) {
+    if (!P || !opts || !out || !lo || !hi || nslices < 1) return fail(NM_EINVAL, "bad argument");
+    CtxScope sc(P->ctx);
+    for (int i = 0; i < nslices; ++i) out[i] = nullptr;
+    std::vector<double> l, u;
+    NM_TRY(slice_lambda(nslices, lo, hi, unit, l, u));
     return lanczos_multi(P, opts, nslices, l.data(), u.data(), out);
+}
+
+int nm_lanczos_begin(nm_problem* P, const nm_slice_opts* opts, int nslices, const double* lo, const double* hi,
+                     nm_unit unit, nm_lanczos** out) {
+    if (!P || !opts || !out) return fail(NM_EINVAL, "null argument");
+    CtxScope sc(P->ctx);
+    *out = nullptr;
+    std::vector<double> l, u;
+    if (nslices == 0) {
+        if (!P->have_interval) return fail(NM_EINVAL, "call nm_set_interval first (or pass the slices)");
+        l.assign(1, P->lo);
+        u.assign(1, P->hi);
+        nslices = 1;
+    } else {
+        if (nslices < 0 || !lo || !hi) return fail(NM_EINVAL, "bad slice list");
+        NM_TRY(slice_lambda(nslices, lo, hi, unit, l, u));
+    }
+    return lanczos_begin(P, opts, nslices, l.data(), u.data(), out);
+}
+
+int nm_lanczos_step(nm_lanczos* L, int* active) {
+    if (!L || !active) return fail(NM_EINVAL, "null argument");
+    CtxScope sc(lanczos_ctx(L));
+    return lanczos_step(L, active);
+}
+
+int nm_lanczos_get_info(const nm_lanczos* L, int slice, nm_lanczos_info* info) {
+    if (!L || !info) return fail(NM_EINVAL, "null argument");
+    return lanczos_state(L, slice, info);
+}
+
+int nm_lanczos_finish(nm_lanczos* L, nm_result** out) {
+    if (!L || !out) return fail(NM_EINVAL, "null argument");
+    CtxScope sc(lanczos_ctx(L));
+    return lanczos_finish(L, out);
+}
+
+int nm_lanczos_free(nm_lanczos* L) {
+    if (!L) return NM_OK;
+    lanczos_free(L);   // touches only the run's own buffers, not its problem
+    return NM_OK;
 }
 
 int nm_ritz(nm_problem* P, nm_ritz_mode mode, const double* V, int64_t ldv, int m, const double* lam_e,

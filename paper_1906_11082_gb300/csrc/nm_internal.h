@@ -126,6 +126,9 @@ struct nm_problem {
     int have_interval = 0;
     double bounds_lo = 0, bounds_hi = 0;
     int have_bounds = 0;
+    // (steps, k_M, seed) of the stored bounds; any option change clears have_bounds
+    int bounds_key_steps = 0, bounds_key_kM = 0;
+    uint64_t bounds_key_seed = 0;
     // kernel timing (nm_profile): event pairs per region kind
     int profile = 0;
     std::vector<cudaEvent_t> ev_pool;

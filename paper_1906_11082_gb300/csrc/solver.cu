@@ -1376,6 +1376,9 @@ int spectrum_bounds(nm_problem* P, int steps, int k_M, uint64_t seed, double* la
     P->bounds_lo = lo;
     P->bounds_hi = hi;
     P->have_bounds = 1;
+    P->bounds_key_steps = steps;
+    P->bounds_key_kM = k_M;
+    P->bounds_key_seed = seed;
     return NM_OK;
 }
 
@@ -1388,54 +1391,90 @@ struct SliceState {
     std::vector<double> Tfull;
     int blocks = 0, m_used = 0;
     bool active = true, converged = false, ok = true;
+    int nwanted = 0, nconv = 0;   // at the last block step
     RRResult rr;
     nm_result* R = nullptr;
 };
 
-// Filtered block Lanczos for S slices in lockstep (S = 1: nm_lanczos_slice).
-// The slices share the spectrum bounds, hence the Chebyshev map (c, e) and
-// the recurrence; their current blocks are filtered together as one block
-// of S b columns with a per-slice gamma in the accumulation. Each slice has
-// its own M-orthonormal basis, two-pass CGS, Cholesky-QR, projected matrix,
-// convergence test and Rayleigh-Ritz, and leaves the batch when done.
-int lanczos_multi(nm_problem* P, const nm_slice_opts* o, int S, const double* lam_lo_in, const double* lam_hi_in,
-                  nm_result** out) {
-    auto t_start = std::chrono::steady_clock::now();
-    nm_ctx* ctx = P->ctx;
-    cudaStream_t s = ctx->stream;
+}  // namespace nm
+
+// A filtered block Lanczos run of S slices in lockstep (S = 1: one slice),
+// advanced one block step at a time. The slices share the spectrum bounds,
+// hence the Chebyshev map (c, e) and the recurrence; their current blocks
+// are filtered together as one block of S b columns with a per-slice gamma
+// in the accumulation. Each slice has its own M-orthonormal basis, two-pass
+// CGS, Cholesky-QR, projected matrix, convergence test and Rayleigh-Ritz,
+// and leaves the batch when done.
+struct nm_lanczos {
+    nm_problem* P = nullptr;
+    nm_slice_opts o{};
+    int S = 0, b = 0, d = 0, k_M = 0, k_P = 0, check = 1, mmax = 0, ldv = 0;
+    double tol = 1e-6, conv_T = 1e-8, blo = 0, bhi = 0, c = 0, e = 0;
+    std::vector<nm::SliceState> st;
+    nm::DevBuf Ycat, Wcat, gtab, fin, fout;
+    double t_filter = 0.0;
+    int j = 0;   // block steps taken
+    std::chrono::steady_clock::time_point t_start;
+};
+
+namespace nm {
+
+int lanczos_begin(nm_problem* P, const nm_slice_opts* o, int S, const double* lam_lo_in, const double* lam_hi_in,
+                  nm_lanczos** out) {
+    *out = nullptr;
     const int b = o->block;
     if (S < 1) return fail(NM_EINVAL, "need at least one slice");
     if (b < 1 || (int64_t)b * S > 64) return fail(NM_EINVAL, "slices x block must be in 1..64");
     if (o->degree < 1) return fail(NM_EINVAL, "degree must be >= 1");
     if (o->max_blocks < 2) return fail(NM_EINVAL, "max_blocks must be >= 2");
-    const int k_M = o->k_M > 0 ? o->k_M : 57;
-    const int k_P = o->k_P > 0 ? o->k_P : 57;
-    const double tol = o->tol > 0 ? o->tol : 1e-6;
-    const int check = o->check_every > 0 ? o->check_every : 1;
-    const int64_t n = P->info.n;
-    const int d = o->degree;
-    double blo, bhi;
-    NM_TRY(spectrum_bounds(P, o->bounds_steps > 0 ? o->bounds_steps : 40, k_M, o->seed + 1, &blo, &bhi));
-    const double conv_T = o->filter_prec == NM_F32 ? 1e-5 : 1e-8;
-    const int mmax = b * o->max_blocks;
-    const int ldv = mmax + b;
-    std::vector<SliceState> st(S);
-    double c = 0, e = 0;
-    for (int q = 0; q < S; ++q) {
-        SliceState& z = st[q];
+    for (int q = 0; q < S; ++q)
         if (!(lam_hi_in[q] > lam_lo_in[q])) return fail(NM_EINVAL, "slice needs lo < hi");
-        z.lam_lo = lam_lo_in[q] <= 0 ? -1e-8 * bhi : lam_lo_in[q];
+    std::unique_ptr<nm_lanczos> L(new (std::nothrow) nm_lanczos());
+    if (!L) return fail(NM_ENOMEM, "host allocation failed");
+    L->t_start = std::chrono::steady_clock::now();
+    cudaStream_t s = P->ctx->stream;
+    L->P = P;
+    L->o = *o;
+    L->o.start = nullptr;
+    L->S = S;
+    L->b = b;
+    L->d = o->degree;
+    L->k_M = o->k_M > 0 ? o->k_M : 57;
+    L->k_P = o->k_P > 0 ? o->k_P : 57;
+    L->tol = o->tol > 0 ? o->tol : 1e-6;
+    L->check = o->check_every > 0 ? o->check_every : 1;
+    L->conv_T = o->filter_prec == NM_F32 ? 1e-5 : 1e-8;
+    L->mmax = b * o->max_blocks;
+    L->ldv = L->mmax + b;
+    const int64_t n = P->info.n;
+    const int d = L->d, ldv = L->ldv;
+    const int bsteps = o->bounds_steps > 0 ? o->bounds_steps : 40;
+    const uint64_t bseed = o->seed + 1;
+    // The bounds depend only on (steps, k_M, seed): a problem keeps the last
+    // estimate and reuses it for the same triple (options reset it).
+    if (P->have_bounds && P->bounds_key_steps == bsteps && P->bounds_key_kM == L->k_M &&
+        P->bounds_key_seed == bseed) {
+        L->blo = P->bounds_lo;
+        L->bhi = P->bounds_hi;
+    } else {
+        NM_TRY(spectrum_bounds(P, bsteps, L->k_M, bseed, &L->blo, &L->bhi));
+    }
+    L->st = std::vector<SliceState>(S);
+    for (int q = 0; q < S; ++q) {
+        SliceState& z = L->st[q];
+        z.lam_lo = lam_lo_in[q] <= 0 ? -1e-8 * L->bhi : lam_lo_in[q];
         z.lam_hi = lam_hi_in[q];
         z.gamma.resize(d + 1);
-        jackson_step_coeffs(blo, bhi, z.lam_lo, z.lam_hi, d, z.gamma.data(), &c, &e);
-        const double pa = cheb_sum(z.gamma, (z.lam_lo - c) / e), pb = cheb_sum(z.gamma, (z.lam_hi - c) / e);
-        z.tau = z.lam_lo > blo ? 0.8 * std::min(pa, pb) : 0.8 * pb;
+        jackson_step_coeffs(L->blo, L->bhi, z.lam_lo, z.lam_hi, d, z.gamma.data(), &L->c, &L->e);
+        const double pa = cheb_sum(z.gamma, (z.lam_lo - L->c) / L->e),
+                     pb = cheb_sum(z.gamma, (z.lam_hi - L->c) / L->e);
+        z.tau = z.lam_lo > L->blo ? 0.8 * std::min(pa, pb) : 0.8 * pb;
         NM_TRY(z.V.alloc((size_t)n * ldv * sizeof(double)));
         NM_TRY(z.MW.alloc((size_t)n * b * sizeof(double)));
         NM_TRY(z.C.alloc((size_t)ldv * b * sizeof(double)));
         NM_TRY(z.H.alloc((size_t)ldv * b * sizeof(double)));
         NM_TRY(z.G.alloc((size_t)b * b * sizeof(double)));
-        z.Tfull.assign((size_t)mmax * mmax, 0.0);
+        z.Tfull.assign((size_t)L->mmax * L->mmax, 0.0);
         // start block: the caller's (same for every slice) or Philox with a per-slice stream
         if (o->start) {
             NM_TRY(launch_scale_copy<double>(n, b, 1.0, o->start, b, z.V.as<double>(), ldv, s));
@@ -1447,114 +1486,157 @@ int lanczos_multi(nm_problem* P, const nm_slice_opts* o, int S, const double* la
         NM_TRY(m_orth(P, z.V.as<double>(), ldv, b, z.MW.as<double>(), z.G.as<double>(), &ok, s));
         if (!ok) return fail(NM_ENOTCONV, "start block is rank deficient in the M inner product");
     }
-    DevBuf Ycat, Wcat, gtab, fin, fout;
-    NM_TRY(Ycat.alloc((size_t)n * S * b * sizeof(double)));
-    NM_TRY(Wcat.alloc((size_t)n * S * b * sizeof(double)));
-    NM_TRY(gtab.alloc((size_t)(d + 1) * S * sizeof(double)));
-    double t_filter = 0.0;
-    for (int j = 0; j < o->max_blocks; ++j) {
-        std::vector<int> act;
-        for (int q = 0; q < S; ++q)
-            if (st[q].active) act.push_back(q);
-        if (act.empty()) break;
-        const int Sa = (int)act.size();
-        const int B = Sa * b;
-        const int m = (j + 1) * b;
-        // gamma table of the active slices and their concatenated current blocks
-        std::vector<double> gt((size_t)(d + 1) * Sa), g0(Sa);
-        for (int g = 0; g < Sa; ++g) {
-            for (int k = 0; k <= d; ++k) gt[(size_t)k * Sa + g] = st[act[g]].gamma[k];
-            NM_TRY(launch_scale_copy<double>(n, b, 1.0, st[act[g]].V.as<double>() + (int64_t)j * b, ldv,
-                                             Ycat.as<double>() + g * b, B, s));
+    NM_TRY(L->Ycat.alloc((size_t)n * S * b * sizeof(double)));
+    NM_TRY(L->Wcat.alloc((size_t)n * S * b * sizeof(double)));
+    NM_TRY(L->gtab.alloc((size_t)(d + 1) * S * sizeof(double)));
+    NM_CUDA(cudaStreamSynchronize(s));
+    *out = L.release();
+    return NM_OK;
+}
+
+int lanczos_active(const nm_lanczos* L) {
+    int a = 0;
+    for (const SliceState& z : L->st) a += z.active ? 1 : 0;
+    return L->j < L->o.max_blocks ? a : 0;
+}
+
+// One block step of every active slice: filter the current blocks, CGS2
+// and Cholesky-QR of each slice's new block, its projected matrix, and,
+// every check_every blocks (or at max_blocks), the convergence test and the
+// Rayleigh-Ritz of the slices whose wanted Ritz values have converged.
+int lanczos_step(nm_lanczos* L, int* active_out) {
+    nm_problem* P = L->P;
+    nm_ctx* ctx = P->ctx;
+    cudaStream_t s = ctx->stream;
+    const nm_slice_opts* o = &L->o;
+    const int64_t n = P->info.n;
+    const int b = L->b, d = L->d, ldv = L->ldv, mmax = L->mmax;
+    const int j = L->j;
+    if (lanczos_active(L) == 0) {
+        *active_out = 0;
+        return NM_OK;
+    }
+    std::vector<int> act;
+    for (int q = 0; q < L->S; ++q)
+        if (L->st[q].active) act.push_back(q);
+    const int Sa = (int)act.size();
+    const int B = Sa * b;
+    const int m = (j + 1) * b;
+    // gamma table of the active slices and their concatenated current blocks
+    std::vector<double> gt((size_t)(d + 1) * Sa);
+    for (int g = 0; g < Sa; ++g) {
+        for (int k = 0; k <= d; ++k) gt[(size_t)k * Sa + g] = L->st[act[g]].gamma[k];
+        NM_TRY(launch_scale_copy<double>(n, b, 1.0, L->st[act[g]].V.as<double>() + (int64_t)j * b, ldv,
+                                         L->Ycat.as<double>() + g * b, B, s));
+    }
+    NM_CUDA(cudaMemcpyAsync(L->gtab.p, gt.data(), gt.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    NM_CUDA(cudaStreamSynchronize(s));
+    auto t0 = std::chrono::steady_clock::now();
+    GammaTable table{L->gtab.as<double>(), gt.data(), Sa, b};
+    NM_TRY(filter_block(P, o->filter_prec, d, L->c, L->e, L->k_M, L->k_P, L->Ycat.as<double>(), B,
+                        L->Wcat.as<double>(), B, &table, L->fin, L->fout, s));
+    NM_CUDA(cudaStreamSynchronize(s));
+    L->t_filter += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int g = 0; g < Sa; ++g) {
+        SliceState& z = L->st[act[g]];
+        double* W = L->Wcat.as<double>() + g * b;   // ld B
+        // CGS2 against the slice's basis in the M inner product
+        NM_CUDA(cudaMemsetAsync(z.H.p, 0, (size_t)m * b * sizeof(double), s));
+        for (int pass = 0; pass < 2; ++pass) {
+            NM_TRY(apply_M_pub<double>(P, W, B, z.MW.as<double>(), b, b, KRON_PLAIN, nullptr, s));
+            NM_TRY(gemm_VtW(ctx, n, m, b, z.V.as<double>(), ldv, z.MW.as<double>(), b, z.C.as<double>(), 0.0));
+            NM_TRY(gemm_WmVC(ctx, n, m, b, -1.0, z.V.as<double>(), ldv, z.C.as<double>(), m, W, B));
+            const double one = 1.0;
+            NM_CUBLAS(cublasDaxpy(ctx->cublas, m * b, &one, z.C.as<double>(), 1, z.H.as<double>(), 1));
         }
-        NM_CUDA(cudaMemcpyAsync(gtab.p, gt.data(), gt.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-        NM_CUDA(cudaStreamSynchronize(s));
-        auto t0 = std::chrono::steady_clock::now();
-        GammaTable table{gtab.as<double>(), gt.data(), Sa, b};
-        NM_TRY(filter_block(P, o->filter_prec, d, c, e, k_M, k_P, Ycat.as<double>(), B, Wcat.as<double>(), B, &table,
-                            fin, fout, s));
-        NM_CUDA(cudaStreamSynchronize(s));
-        t_filter += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        for (int g = 0; g < Sa; ++g) {
-            SliceState& z = st[act[g]];
-            double* W = Wcat.as<double>() + g * b;   // ld B
-            // CGS2 against the slice's basis in the M inner product
-            NM_CUDA(cudaMemsetAsync(z.H.p, 0, (size_t)m * b * sizeof(double), s));
-            for (int pass = 0; pass < 2; ++pass) {
-                NM_TRY(apply_M_pub<double>(P, W, B, z.MW.as<double>(), b, b, KRON_PLAIN, nullptr, s));
-                NM_TRY(gemm_VtW(ctx, n, m, b, z.V.as<double>(), ldv, z.MW.as<double>(), b, z.C.as<double>(), 0.0));
-                NM_TRY(gemm_WmVC(ctx, n, m, b, -1.0, z.V.as<double>(), ldv, z.C.as<double>(), m, W, B));
-                const double one = 1.0;
-                NM_CUBLAS(cublasDaxpy(ctx->cublas, m * b, &one, z.C.as<double>(), 1, z.H.as<double>(), 1));
-            }
-            std::vector<double> hH((size_t)m * b);
-            NM_CUDA(cudaMemcpyAsync(hH.data(), z.H.p, hH.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-            double* Vn = z.V.as<double>() + (int64_t)(j + 1) * b;
-            NM_TRY(launch_scale_copy<double>(n, b, 1.0, W, B, Vn, ldv, s));
-            int ok = 1;
-            NM_TRY(m_orth(P, Vn, ldv, b, z.MW.as<double>(), z.G.as<double>(), &ok, s));
-            z.ok = ok != 0;
-            std::vector<double> hR((size_t)b * b);
-            NM_CUDA(cudaMemcpy(hR.data(), z.G.p, hR.size() * sizeof(double), cudaMemcpyDeviceToHost));
-            for (int cc = 0; cc < b; ++cc)
-                for (int r = 0; r < m; ++r)
-                    z.Tfull[(size_t)r + (size_t)(j * b + cc) * mmax] = hH[(size_t)r + (size_t)cc * m];
-            z.blocks = j + 1;
-            z.m_used = m;
-            std::vector<double> Tm((size_t)m * m);
+        std::vector<double> hH((size_t)m * b);
+        NM_CUDA(cudaMemcpyAsync(hH.data(), z.H.p, hH.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        double* Vn = z.V.as<double>() + (int64_t)(j + 1) * b;
+        NM_TRY(launch_scale_copy<double>(n, b, 1.0, W, B, Vn, ldv, s));
+        int ok = 1;
+        NM_TRY(m_orth(P, Vn, ldv, b, z.MW.as<double>(), z.G.as<double>(), &ok, s));
+        z.ok = ok != 0;
+        std::vector<double> hR((size_t)b * b);
+        NM_CUDA(cudaMemcpy(hR.data(), z.G.p, hR.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int cc = 0; cc < b; ++cc)
             for (int r = 0; r < m; ++r)
-                for (int cc = 0; cc < m; ++cc)
-                    Tm[(size_t)r + (size_t)cc * m] = r <= cc ? z.Tfull[(size_t)r + (size_t)cc * mmax]
-                                                             : z.Tfull[(size_t)cc + (size_t)r * mmax];
-            DevBuf Td, wd;
-            NM_TRY(Td.alloc(Tm.size() * sizeof(double)));
-            NM_TRY(wd.alloc(m * sizeof(double)));
-            NM_CUDA(cudaMemcpy(Td.p, Tm.data(), Tm.size() * sizeof(double), cudaMemcpyHostToDevice));
-            NM_TRY(dense_eig(ctx, m, Td.as<double>(), nullptr, wd.as<double>()));
-            std::vector<double> th(m), Sv((size_t)m * m);
-            NM_CUDA(cudaMemcpy(th.data(), wd.p, m * sizeof(double), cudaMemcpyDeviceToHost));
-            NM_CUDA(cudaMemcpy(Sv.data(), Td.p, Sv.size() * sizeof(double), cudaMemcpyDeviceToHost));
-            int nwanted = 0, nconv = 0;
-            for (int i = 0; i < m; ++i) {
-                if (th[i] < z.tau) continue;
-                ++nwanted;
-                double r2 = 0;
-                if (ok)
-                    for (int r = 0; r < b; ++r) {
-                        double v = 0;
-                        for (int qq = r; qq < b; ++qq)
-                            v += hR[(size_t)r + (size_t)qq * b] * Sv[(size_t)(m - b + qq) + (size_t)i * m];
-                        r2 += v * v;
-                    }
-                if (std::sqrt(r2) <= conv_T * std::max(std::fabs(th[i]), 1.0)) ++nconv;
+                z.Tfull[(size_t)r + (size_t)(j * b + cc) * mmax] = hH[(size_t)r + (size_t)cc * m];
+        z.blocks = j + 1;
+        z.m_used = m;
+        std::vector<double> Tm((size_t)m * m);
+        for (int r = 0; r < m; ++r)
+            for (int cc = 0; cc < m; ++cc)
+                Tm[(size_t)r + (size_t)cc * m] = r <= cc ? z.Tfull[(size_t)r + (size_t)cc * mmax]
+                                                         : z.Tfull[(size_t)cc + (size_t)r * mmax];
+        DevBuf Td, wd;
+        NM_TRY(Td.alloc(Tm.size() * sizeof(double)));
+        NM_TRY(wd.alloc(m * sizeof(double)));
+        NM_CUDA(cudaMemcpy(Td.p, Tm.data(), Tm.size() * sizeof(double), cudaMemcpyHostToDevice));
+        NM_TRY(dense_eig(ctx, m, Td.as<double>(), nullptr, wd.as<double>()));
+        std::vector<double> th(m), Sv((size_t)m * m);
+        NM_CUDA(cudaMemcpy(th.data(), wd.p, m * sizeof(double), cudaMemcpyDeviceToHost));
+        NM_CUDA(cudaMemcpy(Sv.data(), Td.p, Sv.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        int nwanted = 0, nconv = 0;
+        for (int i = 0; i < m; ++i) {
+            if (th[i] < z.tau) continue;
+            ++nwanted;
+            double r2 = 0;
+            if (ok)
+                for (int r = 0; r < b; ++r) {
+                    double v = 0;
+                    for (int qq = r; qq < b; ++qq)
+                        v += hR[(size_t)r + (size_t)qq * b] * Sv[(size_t)(m - b + qq) + (size_t)i * m];
+                    r2 += v * v;
+                }
+            if (std::sqrt(r2) <= L->conv_T * std::max(std::fabs(th[i]), 1.0)) ++nconv;
+        }
+        z.nwanted = nwanted;
+        z.nconv = nconv;
+        if (o->log_every > 0 && (j + 1) % o->log_every == 0)
+            fprintf(stderr, "[nm] slice %d block %d m=%d wanted=%d converged=%d filter %.1fs total %.1fs\n", act[g],
+                    j + 1, m, nwanted, nconv, L->t_filter,
+                    std::chrono::duration<double>(std::chrono::steady_clock::now() - L->t_start).count());
+        const bool last = j + 1 == o->max_blocks || !ok;
+        if ((nwanted > 0 && nconv == nwanted && (j + 1) % L->check == 0) || last) {
+            if (!z.R) {
+                z.R = new (std::nothrow) nm_result();
+                if (!z.R) return fail(NM_ENOMEM, "host allocation failed");
             }
-            if (o->log_every > 0 && (j + 1) % o->log_every == 0)
-                fprintf(stderr, "[nm] slice %d block %d m=%d wanted=%d converged=%d filter %.1fs total %.1fs\n", act[g],
-                        j + 1, m, nwanted, nconv, t_filter,
-                        std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
-            const bool last = j + 1 == o->max_blocks || !ok;
-            if ((nwanted > 0 && nconv == nwanted && (j + 1) % check == 0) || last) {
-                if (!z.R) {
-                    z.R = new (std::nothrow) nm_result();
-                    if (!z.R) return fail(NM_ENOMEM, "host allocation failed");
-                }
-                NM_TRY(rayleigh_ritz(P, z.V.as<double>(), ldv, m, z.lam_lo, z.lam_hi, &z.R->X, z.rr));
-                bool all = z.rr.k > 0;
-                for (double r : z.rr.res) all = all && r <= tol;
-                if (all || last) {
-                    z.converged = all;
-                    z.active = false;
-                }
+            NM_TRY(rayleigh_ritz(P, z.V.as<double>(), ldv, m, z.lam_lo, z.lam_hi, &z.R->X, z.rr));
+            bool all = z.rr.k > 0;
+            for (double r : z.rr.res) all = all && r <= L->tol;
+            if (all || last) {
+                z.converged = all;
+                z.active = false;
             }
         }
     }
+    L->j = j + 1;
+    *active_out = lanczos_active(L);
+    return NM_OK;
+}
+
+// Results of every slice (a Rayleigh-Ritz on the current basis of the
+// slices that have none yet). NM_ENOTCONV if a slice did not pass tol; the
+// results are returned all the same. Ownership of the results moves to the
+// caller; the run keeps no reference to them.
+int lanczos_finish(nm_lanczos* L, nm_result** out) {
+    nm_problem* P = L->P;
+    const int64_t n = P->info.n;
+    for (int q = 0; q < L->S; ++q) out[q] = nullptr;
     int rc = NM_OK;
-    for (int q = 0; q < S; ++q) {
-        SliceState& z = st[q];
+    for (int q = 0; q < L->S; ++q) {
+        SliceState& z = L->st[q];
         if (!z.R) {
             z.R = new (std::nothrow) nm_result();
             if (!z.R) return fail(NM_ENOMEM, "host allocation failed");
-            NM_TRY(rayleigh_ritz(P, z.V.as<double>(), ldv, z.m_used, z.lam_lo, z.lam_hi, &z.R->X, z.rr));
+            if (z.m_used > 0) {
+                NM_TRY(rayleigh_ritz(P, z.V.as<double>(), L->ldv, z.m_used, z.lam_lo, z.lam_hi, &z.R->X, z.rr));
+            } else {
+                // no block step taken: the start block is the basis
+                NM_TRY(rayleigh_ritz(P, z.V.as<double>(), L->ldv, L->b, z.lam_lo, z.lam_hi, &z.R->X, z.rr));
+                z.m_used = L->b;
+            }
         }
         nm_result* R = z.R;
         R->lambda = z.rr.lam;
@@ -1563,16 +1645,58 @@ int lanczos_multi(nm_problem* P, const nm_slice_opts* o, int S, const double* la
         R->info.n = n;
         R->info.blocks = z.blocks;
         R->info.m = z.m_used;
-        R->info.filter_applications = (int64_t)z.blocks * b;
-        R->info.lam_lo = blo;
-        R->info.lam_hi = bhi;
-        R->info.seconds_filter = t_filter;
-        R->info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-        out[q] = R;
+        R->info.filter_applications = (int64_t)z.blocks * L->b;
+        R->info.lam_lo = L->blo;
+        R->info.lam_hi = L->bhi;
+        R->info.seconds_filter = L->t_filter;
+        R->info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - L->t_start).count();
         if (!z.converged) rc = NM_ENOTCONV;
+    }
+    for (int q = 0; q < L->S; ++q) {
+        out[q] = L->st[q].R;
+        L->st[q].R = nullptr;
     }
     if (rc != NM_OK) return fail(rc, "a slice did not converge within max_blocks");
     return NM_OK;
+}
+
+int lanczos_state(const nm_lanczos* L, int slice, nm_lanczos_info* out) {
+    if (slice < 0 || slice >= L->S) return fail(NM_EINVAL, "slice index out of range");
+    const SliceState& z = L->st[slice];
+    out->blocks = z.blocks;
+    out->m = z.m_used;
+    out->active = z.active && L->j < L->o.max_blocks ? 1 : 0;
+    out->converged = z.converged ? 1 : 0;
+    out->wanted = z.nwanted;
+    out->ritz_converged = z.nconv;
+    out->seconds_filter = L->t_filter;
+    return NM_OK;
+}
+
+nm_ctx* lanczos_ctx(const nm_lanczos* L) { return L->P->ctx; }
+
+void lanczos_free(nm_lanczos* L) {
+    if (!L) return;
+    for (SliceState& z : L->st) {
+        delete z.R;
+        z.R = nullptr;
+    }
+    delete L;
+}
+
+// Filtered block Lanczos for S slices in lockstep (S = 1: nm_lanczos_slice):
+// begin, block steps until no slice is active, finish.
+int lanczos_multi(nm_problem* P, const nm_slice_opts* o, int S, const double* lam_lo_in, const double* lam_hi_in,
+                  nm_result** out) {
+    for (int q = 0; q < S; ++q) out[q] = nullptr;
+    nm_lanczos* L = nullptr;
+    int rc = lanczos_begin(P, o, S, lam_lo_in, lam_hi_in, &L);
+    if (rc != NM_OK) return rc;
+    int active = 1;
+    while (active > 0 && rc == NM_OK) rc = lanczos_step(L, &active);
+    if (rc == NM_OK) rc = lanczos_finish(L, out);
+    lanczos_free(L);
+    return rc;
 }
 
 int lanczos_slice(nm_problem* P, const nm_slice_opts* o, nm_result** out) {

@@ -30,7 +30,8 @@ EXPORTS = (
     "nm_spectrum_bounds", "nm_filter_design", "nm_filter_apply", "nm_lanczos_slice", "nm_ritz",
     "nm_result_get_info", "nm_result_values", "nm_result_vectors", "nm_result_free",
     "nm_profile", "nm_profile_read", "nm_kernel_launches", "nm_set_option", "nm_autotune",
-    "nm_lanczos_multi", "nm_filter_apply_static",
+    "nm_lanczos_multi", "nm_filter_apply_static", "nm_lanczos_begin", "nm_lanczos_step",
+    "nm_lanczos_get_info", "nm_lanczos_finish", "nm_lanczos_free",
 )
 
 
@@ -68,6 +69,11 @@ class nm_slice_opts(C.Structure):
                 ("max_blocks", C.c_int32), ("check_every", C.c_int32), ("filter_prec", C.c_int32),
                 ("tol", C.c_double), ("seed", C.c_uint64), ("start", C.c_void_p),
                 ("bounds_steps", C.c_int32), ("log_every", C.c_int32)]
+
+
+class nm_lanczos_info(C.Structure):
+    _fields_ = [("blocks", C.c_int32), ("m", C.c_int32), ("active", C.c_int32), ("converged", C.c_int32),
+                ("wanted", C.c_int32), ("ritz_converged", C.c_int32), ("seconds_filter", C.c_double)]
 
 
 class nm_result_info(C.Structure):
@@ -111,6 +117,11 @@ def _load():
         "nm_autotune": [vp, i32, i32, i32, C.c_char_p, i32],
         "nm_lanczos_multi": [vp, C.POINTER(nm_slice_opts), i32, vp, vp, i32, vp],
         "nm_filter_apply_static": [vp, C.POINTER(nm_filter), vp, i64, vp, i64, i32, vp],
+        "nm_lanczos_begin": [vp, C.POINTER(nm_slice_opts), i32, vp, vp, i32, C.POINTER(vp)],
+        "nm_lanczos_step": [vp, C.POINTER(i32)],
+        "nm_lanczos_get_info": [vp, i32, C.POINTER(nm_lanczos_info)],
+        "nm_lanczos_finish": [vp, vp],
+        "nm_lanczos_free": [vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -187,7 +198,9 @@ class Context:
 
     def close(self):
         if self.h:
-            for ch in list(self._children):
+            # runs before results before problems: a run borrows its problem
+            order = {"LanczosRun": 0, "Result": 1}
+            for ch in sorted(self._children, key=lambda o: order.get(type(o).__name__, 2)):
                 ch.free()
             _lib.nm_ctx_destroy(self.h)
             self.h = None
@@ -396,6 +409,23 @@ class Problem:
             _check(rc, self.ctx.h)
         return res
 
+    def lanczos_begin(self, slices=None, unit=NM_UNIT_OMEGA, block=16, degree=100, k_M=0, k_P=0, max_blocks=40,
+                      check_every=1, prec=NM_F64, tol=1e-6, seed=1, start=None, bounds_steps=40, log_every=0):
+        """Begin a resumable filtered block Lanczos run (nm_lanczos_begin):
+        slices=None solves the interval of set_interval, else [(lo, hi), ...]."""
+        o = nm_slice_opts(block, degree, k_M, k_P, max_blocks, check_every, prec, tol, seed,
+                          C.c_void_p(start.data_ptr()) if start is not None else None, bounds_steps, log_every)
+        if slices is None:
+            S, lo, hi = 0, None, None
+        else:
+            S = len(slices)
+            lo = np.ascontiguousarray([s[0] for s in slices], np.float64)
+            hi = np.ascontiguousarray([s[1] for s in slices], np.float64)
+        h = C.c_void_p()
+        _check(_lib.nm_lanczos_begin(self.h, C.byref(o), S, lo.ctypes.data_as(C.c_void_p) if S else None,
+                                     hi.ctypes.data_as(C.c_void_p) if S else None, unit, C.byref(h)), self.ctx.h)
+        return LanczosRun(self, h, max(S, 1))
+
     def ritz(self, V, mode=NM_RITZ_PENCIL, lam_e=None):
         m = V.shape[1]
         le = None if lam_e is None else np.ascontiguousarray(lam_e, np.float64)
@@ -427,6 +457,50 @@ class Problem:
         if getattr(self, "h", None):
             if self.ctx.h:
                 _lib.nm_problem_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class LanczosRun:
+    """A resumable block Lanczos run (nm_lanczos_begin / step / finish)."""
+
+    def __init__(self, prob, h, nslices):
+        self.prob = prob
+        self.h = h
+        self.nslices = nslices
+        prob.ctx._adopt(self)
+
+    def step(self):
+        """One block step; returns the number of slices still active."""
+        a = C.c_int()
+        _check(_lib.nm_lanczos_step(self.h, C.byref(a)), self.prob.ctx.h)
+        return a.value
+
+    def info(self, slice=0):
+        st = nm_lanczos_info()
+        _check(_lib.nm_lanczos_get_info(self.h, slice, C.byref(st)), self.prob.ctx.h)
+        return {k: getattr(st, k) for k, _ in nm_lanczos_info._fields_}
+
+    def finish(self, allow_unconverged=False):
+        """Results of every slice (list of Result); frees the run."""
+        hs = (C.c_void_p * self.nslices)()
+        rc = _lib.nm_lanczos_finish(self.h, C.cast(hs, C.c_void_p))
+        res = [Result(self.prob.ctx, C.c_void_p(h)) for h in hs if h]
+        self.free()
+        if rc != NM_OK and not (rc == NM_ENOTCONV and allow_unconverged and len(res) == self.nslices):
+            for r in res:
+                r.free()
+            _check(rc, self.prob.ctx.h)
+        return res
+
+    def free(self):
+        if self.h:
+            _lib.nm_lanczos_free(self.h)
             self.h = None
 
     def __del__(self):

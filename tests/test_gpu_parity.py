@@ -587,3 +587,85 @@ def test_lanczos_multi_rejects_too_wide(nm, ball):
     with pytest.raises(nm.NMError) as e:
         P.lanczos_multi([(0.0, 1.0)] * 5, block=16)
     assert e.value.code == nm.NM_EINVAL
+
+
+# ------------------------------------------------------------------ resumable block Lanczos
+def test_lanczos_steps_equal_slice_call(nm, ball):
+    """begin / step until no slice is active / finish computes what
+    nm_lanczos_slice computes (same kernels in the same order: identical
+    eigenvalues), and the result matches the dense oracle."""
+    w, S, P = ball
+    P.set_interval(0.0, 3.0)
+    kw = dict(block=8, degree=100, k_M=40, k_P=40, max_blocks=16, seed=5, check_every=2)
+    whole = P.lanczos_slice(**kw)
+    run = P.lanczos_begin(None, **kw)
+    steps = 0
+    while True:
+        st = run.info(0)
+        assert st["blocks"] == steps and st["active"] == 1
+        active = run.step()
+        steps += 1
+        if active == 0:
+            break
+        assert steps < 16
+    st = run.info(0)
+    assert st["converged"] == 1 and st["active"] == 0 and st["blocks"] == steps
+    res = run.finish()[0]
+    assert res.info["blocks"] == whole.info["blocks"] == steps
+    assert np.array_equal(res.lam, whole.lam)
+    K, M = eig.pencil_dense(S)
+    lam = eig.all_eigs(K, M)[0]
+    _check_slice(res, lam[(lam >= -1e-8 * lam[-1]) & (lam <= 9.0)], lam[-1])
+
+
+def test_lanczos_steps_two_slices_and_early_finish(nm, ball):
+    """Two slices in one run (mixed form) step to the dense oracle's
+    eigenpairs; finishing a run early returns Rayleigh-Ritz pairs of the
+    current basis with NM_ENOTCONV; a step after the end is a no-op."""
+    w, S, P = ball
+    K, M = eig.pencil_dense(S)
+    lam = eig.all_eigs(K, M)[0]
+    slices = [(0.0, 2.7), (2.7, 3.0)]
+    run = P.lanczos_begin(slices, block=8, degree=100, k_M=20, k_P=20, max_blocks=16, seed=4,
+                          prec=nm.NM_MIXED)
+    while run.step() > 0:
+        pass
+    assert run.step() == 0
+    res = run.finish()
+    for (lo, hi), r in zip(slices, res):
+        l = -1e-8 * lam[-1] if lo == 0 else lo * lo
+        _check_slice(r, lam[(lam >= l) & (lam <= hi * hi)], lam[-1])
+    P.set_interval(0.0, 3.0)
+    early = P.lanczos_begin(None, block=8, degree=100, k_M=40, k_P=40, max_blocks=16, seed=5)
+    early.step()
+    with pytest.raises(nm.NMError) as e:
+        early.finish()
+    assert e.value.code == nm.NM_ENOTCONV
+    early = P.lanczos_begin(None, block=8, degree=100, k_M=40, k_P=40, max_blocks=16, seed=5)
+    early.step()
+    part = early.finish(allow_unconverged=True)[0]
+    assert part.info["blocks"] == 1 and part.info["m"] == 8
+    # abandoning a run without finishing it releases it
+    P.lanczos_begin(None, block=8, degree=100, k_M=40, k_P=40, max_blocks=16, seed=5).free()
+
+
+def test_lanczos_begin_reuses_bounds(nm, ball):
+    """The spectrum bounds depend on (steps, k_M, seed); a second run with
+    the same triple reuses them (identical lam_lo, lam_hi), and an option
+    change makes the next run compute them again."""
+    w, S, P = ball
+    P.set_interval(0.0, 3.0)
+    kw = dict(block=8, degree=60, k_M=40, k_P=40, max_blocks=4, seed=9)
+    r1 = P.lanczos_begin(None, **kw)
+    r1.step()
+    a = r1.finish(allow_unconverged=True)[0]
+    r2 = P.lanczos_begin(None, **kw)
+    r2.step()
+    b = r2.finish(allow_unconverged=True)[0]
+    assert a.info["lam_lo"] == b.info["lam_lo"] and a.info["lam_hi"] == b.info["lam_hi"]
+    np.testing.assert_array_equal(a.lam, b.lam)
+    P.set_option("vec", 1)
+    r3 = P.lanczos_begin(None, **kw)
+    r3.step()
+    c = r3.finish(allow_unconverged=True)[0]
+    assert c.info["lam_hi"] == pytest.approx(a.info["lam_hi"], rel=1e-10)
