@@ -201,6 +201,74 @@ def test_lamb_toroidal_is_first_root_of_bessel_relation():
     assert abs(x0 - lamb_modes(3.0)[0][0]) < 1e-6
 
 
+def _traction_at_surface(l, kind, vp=1.7, vs=1.0, rho=1.0, th0=0.7):
+    """Surface traction of Cartesian displacement fields built from potentials.
+
+    A field independent of the radial functions in oracle/lamb.py: for a
+    homogeneous ball the displacement is grad(phi) (P), curl curl(x psi)
+    (S) or curl(x chi) (T) with phi, psi, chi = j_l(kappa r) P_l(cos theta)
+    (Navier's equation holds for kappa = w / Vp or w / Vs); the traction
+    sigma . r_hat at r = 1, theta = th0 is formed by symbolic Cartesian
+    differentiation (sympy). Returns callables of w giving the (r, theta,
+    phi) traction components for each field."""
+    sp = pytest.importorskip("sympy")
+    x, y, z, w = sp.symbols('x y z w', real=True)
+    r = sp.sqrt(x * x + y * y + z * z)
+    X = sp.Matrix([x, y, z])
+    s = sp.Symbol('s')
+    jl = sp.sin(s) / s
+    for _ in range(l):
+        jl = sp.diff(jl, s) / s
+    jl = (-s) ** l * jl                     # Rayleigh's formula for j_l
+
+    def pot(kk):
+        return jl.subs(s, kk * r) * sp.legendre(l, z / r)
+
+    def grad(f):
+        return sp.Matrix([sp.diff(f, v) for v in (x, y, z)])
+
+    def curl(F):
+        return sp.Matrix([sp.diff(F[2], y) - sp.diff(F[1], z), sp.diff(F[0], z) - sp.diff(F[2], x),
+                          sp.diff(F[1], x) - sp.diff(F[0], y)])
+
+    mu = rho * vs * vs
+    lam = rho * vp * vp - 2 * mu
+    h, k = w / vp, w / vs
+    fields = {"S": [grad(pot(h)), curl(curl(X * pot(k)))], "T": [curl(X * pot(k))], "R": [grad(pot(h))]}[kind]
+    pt = {x: sp.sin(th0), y: 0, z: sp.cos(th0)}
+    frame = (sp.Matrix([sp.sin(th0), 0, sp.cos(th0)]), sp.Matrix([sp.cos(th0), 0, -sp.sin(th0)]),
+             sp.Matrix([0, 1, 0]))
+    out = []
+    for u in fields:
+        J = u.jacobian(X)
+        sig = lam * J.trace() * sp.eye(3) + mu * (J + J.T)
+        t = (sig * X / r).subs(pt)
+        out.append([sp.lambdify(w, (t.T * e)[0], 'mpmath') for e in frame])
+    return out
+
+
+def test_lamb_modes_from_independent_potential_fields():
+    """The closed-form Lamb frequencies (oracle/lamb.py, radial functions U,
+    V) are roots of the traction-free condition formed from 3-D Cartesian
+    potential fields instead: the 2 x 2 traction determinant of the P and S
+    fields (spheroidal), the phi traction of the T field (toroidal) and the
+    radial traction of the P field (l = 0)."""
+    import mpmath
+    mpmath.mp.dps = 30
+    modes = {lab: om for om, lab, _ in lamb_modes(6.0)}
+    for lab, l, kind in (("0T2", 2, "T"), ("0S2", 2, "S"), ("1S1", 1, "S"), ("0S0", 0, "R"), ("0T3", 3, "T"),
+                         ("1S2", 2, "S")):
+        f = _traction_at_surface(l, kind)
+        if kind == "S":
+            g = lambda w: float(f[0][0](w) * f[1][1](w) - f[1][0](w) * f[0][1](w))
+        elif kind == "T":
+            g = lambda w: float(f[0][2](w))
+        else:
+            g = lambda w: float(f[0][0](w))
+        root = brentq(g, modes[lab] - 0.03, modes[lab] + 0.03, xtol=1e-14)
+        assert root == pytest.approx(modes[lab], rel=1e-12), lab
+
+
 def test_ball_converges_to_lamb():
     """0T2 and 0S2 multiplet means approach Lamb's values under refinement."""
     exact = {m[1]: m[0] for m in lamb_modes(3.0)}
@@ -294,25 +362,62 @@ def test_cowling_homogeneous_ball_rigid_motions():
 
 def test_layered_cowling_spectrum_structure():
     """Three-layer planet, Cowling: K_eff symmetric; the only clearly
-    negative modes are the three inner-core translations (a dense inner core
-    in a lighter fluid has no self-gravity restoring force without S(u));
-    a large near-zero cluster comes from the fluid (essential spectrum)."""
+    negative modes are three near-rigid rotations of the inner core
+    (rigid rotations in a radial field cost nothing; the direct-summation
+    field's non-radial error on the coarse 0.19-radius core makes them
+    slightly negative, and it shrinks under refinement, see below); a large
+    near-zero cluster comes from the fluid (essential spectrum)."""
     mesh, model = layered_planet(h=0.25, seed=7)
     S = fem.assemble(mesh, model)
     assert abs(S.A_G - S.A_G.T).max() <= 1e-13 * abs(S.A_G).max()
     K = fem.k_eff_dense(S)
-    lam, X = eig.all_eigs(K, S.M.toarray())
+    M = S.M.toarray()
+    lam, X = eig.all_eigs(K, M)
     neg = np.nonzero(lam < -0.01)[0]
     assert len(neg) == 3
     ns = int((S.dm.unode_solid >= 0).sum())
-    r = np.linalg.norm(S.node_xyz[S.dm.u_p2], axis=1)
-    ic = (r < 0.19 + 1e-9) & (np.arange(len(r)) < ns)
-    md = S.M_rho.diagonal()
+    x = S.node_xyz[S.dm.u_p2]
+    ic = (np.linalg.norm(x, axis=1) < 0.19 + 1e-9) & (np.arange(len(x)) < ns)
+    rot = []
+    for axis in np.eye(3):
+        u = np.zeros((len(x), 3))
+        u[ic] = np.cross(axis, x[ic])
+        rot.append(u.ravel())
+    rot = np.stack(rot, 1)
     for i in neg:
-        u = X[:, i].reshape(-1, 3)
-        e = (u * u).sum(1) * md
-        assert e[ic].sum() > 0.9 * e.sum()
+        v = X[:, i]
+        r = v - rot @ np.linalg.lstsq(rot, v, rcond=None)[0]
+        assert r @ M @ r <= 0.01 * (v @ M @ v)
     assert (np.abs(lam) < 0.01).sum() > 0.2 * S.dm.Np
+
+
+def test_layered_rigid_rotations_cost_nothing_under_refinement():
+    """Rigid rotations of a spherically symmetric planet in its own radial
+    reference field are zero-energy motions of K_eff (Sec. 2.3: no strain,
+    u.g' = 0, and the gravity derivative terms cancel). With the
+    direct-summation field of a polyhedral mesh their Rayleigh quotients,
+    small against the gravity scale (4/3) pi G rho ~ 1.3, fall under
+    refinement: for the whole planet (K_eff) and for the inner core alone
+    (A_G: the solid and interface gravity terms)."""
+    out = []
+    for h in (0.25, 0.15):
+        mesh, model = layered_planet(h=h, seed=7)
+        S = fem.assemble(mesh, model)
+        ns = int((S.dm.unode_solid >= 0).sum())
+        x = S.node_xyz[S.dm.u_p2]
+        ic = (np.linalg.norm(x, axis=1) < 0.19 + 1e-9) & (np.arange(len(x)) < ns)
+        whole, core = [], []
+        for axis in np.eye(3):
+            u = np.cross(axis, x).ravel()
+            whole.append(abs(u @ fem.k_eff_apply(S, u[:, None]).ravel()) / (u @ (S.M @ u)))
+            v = np.zeros((len(x), 3))
+            v[ic] = np.cross(axis, x[ic])
+            v = v.ravel()
+            core.append(abs(v @ (S.A_G @ v)) / (v @ (S.M @ v)))
+        out.append((max(whole), max(core)))
+    (w0, c0), (w1, c1) = out
+    assert w1 < w0 < 5e-3
+    assert c1 < 0.1 * c0 and c1 < 0.01
 
 
 def test_gravity_direct_summation_homogeneous_ball():
@@ -465,3 +570,157 @@ def test_rotating_reduction_identities():
     off = G - np.diag(np.diag(G))
     assert np.abs(off).max() <= 1e-10 * np.abs(np.diag(G)).max()
     assert (np.diag(G).real > 0).all()
+
+
+# ------------------------------------------------------------ gravity terms with a prescribed field
+def _two_layer(h, rho_s, rho_f, kap_f=1.0, mu_s=1.0, lam_s=2.0, N2=0.0, r_core=0.5):
+    """Solid core (radius r_core) inside a fluid shell, homogeneous layers."""
+    m = layered_ball(radii=(r_core, 1.0), h=h, fluid_layers=(1,), seed=5)
+    fl = m.region == 1
+    nt = m.nt
+    mdl = Model(rho=np.where(fl, rho_f, rho_s), lam=np.where(fl, kap_f, lam_s), mu=np.where(fl, 0.0, mu_s),
+                N2=np.where(fl, N2, 0.0), G=0.0, Omega=np.zeros(3))
+    return m, mdl
+
+
+def _p2_nodes(m):
+    dm = fem.dof_map(m.tet, m.region, m.nv)
+    return dm, fem.p2_coords(m.xyz, dm.edges)
+
+
+def test_core_buoyancy_closed_form():
+    """Archimedes in a fixed linear field g' = -gamma x (Cowling, Sec. 2.3).
+
+    Translating a homogeneous solid core rigidly by a inside a fluid of
+    density rho_f costs, in the solid gravity volume terms,
+    rho_s gamma V |a|^2 (from -rho u.(grad g').v; the two other terms vanish
+    for a constant field), and in the fluid-solid interface term
+    S{(v.g')(nu.u) rho_f}, by the divergence theorem over the core,
+    rho_f int_core a.grad(a.g') = -rho_f gamma V |a|^2. With g' linear the
+    P2 interpolants of the nodal products are exact, so
+    a^T A_G a / a^T M a = gamma (1 - rho_f / rho_s) to rounding. A dropped
+    interface term gives gamma, a flipped one gamma (1 + rho_f/rho_s), the
+    solid density in place of the fluid one 0. Rigid rotations of the core
+    cost nothing (u.g' = 0 and the two derivative terms cancel)."""
+    gamma, rho_s, rho_f = 1.7, 2.6, 1.9
+    m, mdl = _two_layer(0.3, rho_s, rho_f)
+    dm, x = _p2_nodes(m)
+    S = fem.assemble(m, mdl, gprime=-gamma * x)
+    ns = int((dm.unode_solid >= 0).sum())
+    xs = S.node_xyz[S.dm.u_p2[:ns]]
+    for a in (np.array([1.0, 0.0, 0.0]), np.array([0.3, -0.8, 0.5])):
+        u = np.zeros((S.dm.Nu, 3))
+        u[:ns] = a
+        u = u.ravel()
+        ray = u @ (S.A_G @ u) / (u @ (S.M @ u))
+        assert ray == pytest.approx(gamma * (1.0 - rho_f / rho_s), rel=1e-10)
+    for axis in np.eye(3):
+        u = np.zeros((S.dm.Nu, 3))
+        u[:ns] = np.cross(axis, xs)
+        u = u.ravel()
+        assert abs(u @ (S.A_G @ u)) <= 1e-12 * abs(S.A_G).max() * (u @ u)
+
+
+def test_fluid_buoyancy_matrix_for_a_constant_field():
+    """With a constant field g' = c the fluid buoyancy term
+    int rho N^2 (g'.v)(g'.u) / |g'|^2 is N^2 M_rho (x) c c^T / |c|^2 exactly
+    (the direction enters, not the magnitude: |c| = 2.5 here). A fluid ball
+    has no other A_G term."""
+    c = np.array([1.5, -2.0, 0.0])
+    N2 = 0.04
+    m = layered_ball(radii=(1.0,), h=0.45, fluid_layers=(0,), seed=3)
+    nt = m.nt
+    mdl = Model(rho=np.full(nt, 1.3), lam=np.full(nt, 2.0), mu=np.zeros(nt), N2=np.full(nt, N2), G=0.0,
+                Omega=np.zeros(3))
+    dm, x = _p2_nodes(m)
+    S = fem.assemble(m, mdl, gprime=np.tile(c, (len(x), 1)))
+    ch = c / np.linalg.norm(c)
+    ref = sps_kron(S.M_rho, N2 * np.outer(ch, ch))
+    assert abs(S.A_G - ref).max() <= 1e-13 * abs(ref).max()
+
+
+def sps_kron(A, B):
+    import scipy.sparse as sps
+    return sps.kron(A, sps.csr_matrix(B), format="csr")
+
+
+def test_fluid_pressure_gravity_coupling_by_quadrature():
+    """E_G in a fluid ball (eq. weakfluid2: int v.grad p - (v.g') p rho / kappa)
+    against an independent Gauss rule on every tet: for a constant field c,
+    a linear displacement u and a quadratic pressure q (all exact in P2),
+    q^T E_G^T u = int u.grad q - (rho / kappa) (u.c) q. A dropped or flipped
+    gravity part, or rho and kappa exchanged, moves it by O(1)."""
+    rng = np.random.default_rng(4)
+    c = np.array([0.7, -1.1, 0.4])
+    rho, kap = 1.4, 2.3
+    m = layered_ball(radii=(1.0,), h=0.45, fluid_layers=(0,), seed=3)
+    nt = m.nt
+    mdl = Model(rho=np.full(nt, rho), lam=np.full(nt, kap), mu=np.zeros(nt), N2=np.zeros(nt), G=0.0,
+                Omega=np.zeros(3))
+    dm, x = _p2_nodes(m)
+    S = fem.assemble(m, mdl, gprime=np.tile(c, (len(x), 1)))
+    A = rng.standard_normal((3, 3))
+    b = rng.standard_normal(3)
+    Qm = rng.standard_normal((3, 3))
+    Qm = Qm + Qm.T
+    qv = rng.standard_normal(3)
+    ufun = lambda p: p @ A.T + b                       # linear vector field
+    qfun = lambda p: np.einsum('ni,ij,nj->n', p, Qm, p) + p @ qv + 0.3
+    dq = lambda p: 2.0 * p @ Qm + qv
+    xu = S.node_xyz[S.dm.u_p2]
+    xp = S.node_xyz[np.nonzero(S.dm.pnode >= 0)[0][np.argsort(S.dm.pnode[S.dm.pnode >= 0])]]
+    lhs = qfun(xp) @ (S.E_G.T @ ufun(xu).ravel())
+    pts, wts = _duffy_rule(4)
+    total = 0.0
+    for t in m.tet:
+        v = m.xyz[t]
+        J = (v[1:] - v[0]).T
+        det = abs(np.linalg.det(J))
+        p = v[0] + pts @ J.T
+        uu = ufun(p)
+        f = (uu * dq(p)).sum(1) - (rho / kap) * (uu @ c) * qfun(p)
+        total += det * (wts @ f)
+    assert lhs == pytest.approx(total, rel=1e-11)
+
+
+# ------------------------------------------------------------ eigenvalue counts and the rotating reduction
+def test_inertia_counts_pin_the_slice_count():
+    """Sylvester's law: the number of eigenvalues of (K_eff, M) in
+    [s1, s2) is the difference of the negative inertia of K_eff - s M at
+    the two edges (LDL^T, another factorisation than the dense eigensolve)."""
+    mesh, model = layered_planet(h=0.35, seed=7)
+    S = fem.assemble(mesh, model)
+    K, M = eig.pencil_dense(S)
+    lam = eig.all_eigs(K, M)[0]
+    for s1, s2 in ((16.0, 30.0), (30.0, 42.0)):
+        # edges in gaps of the dense spectrum
+        s1 = 0.5 * (lam[lam < s1].max() + lam[lam >= s1].min())
+        s2 = 0.5 * (lam[lam < s2].max() + lam[lam >= s2].min())
+        n_dense = int(((lam >= s1) & (lam < s2)).sum())
+        assert n_dense > 0
+        assert eig.inertia_count(K, M, s2) - eig.inertia_count(K, M, s1) == n_dense
+
+
+def test_rotating_reduction_converges_to_full_problem():
+    """The projected rotating problem (eq. sublinear0) on the m_e lowest
+    eigenvectors approaches the full linearised quadratic problem (Sec. 7)
+    as m_e grows, and equals it when the basis is complete. K is shifted by
+    M (K + M is positive definite; both problems use the same shifted K)."""
+    w = config_ball()
+    model = w.model
+    model.Omega = np.array([0.0, 0.0, 0.3])
+    S = fem.assemble(w.mesh, model)
+    K, M = eig.pencil_dense(S)
+    K = K + M
+    R = S.R.toarray()
+    full = np.sort(eig.rotating_full(K, M, R))
+    lam, X = eig.all_eigs(K, M)
+    target = full[full > 0][:12]
+    errs = []
+    for me in (20, 60, 200, len(lam)):
+        Xe = X[:, :me]
+        wr, _ = eig.rotating_reduced(lam[:me], Xe.T @ R @ Xe)
+        got = np.sort(wr[wr > 0])[:12]
+        errs.append(np.abs(got / target - 1).max())
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+    assert errs[3] <= 1e-10
