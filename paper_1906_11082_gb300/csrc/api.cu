@@ -226,6 +226,11 @@ int nm_set_option(nm_problem* P, const char* key, int64_t value) {
         P->use_sched = (int)value;
         return NM_OK;
     }
+    if (std::string(key) == "tma") {
+        if (value != 0 && value != 1) return fail(NM_EINVAL, "tma must be 0 or 1");
+        P->use_tma = (int)value;
+        return NM_OK;
+    }
     if (std::string(key) == "vec") {
         if (value != 0 && value != 1) return fail(NM_EINVAL, "vec must be 0 or 1");
         P->use_vec = (int)value;

@@ -663,6 +663,8 @@ template <typename T>
 int launch_kron(int R, int mode, const KronArgs<T>& a, cudaStream_t s) {
     if (a.b < 1 || a.b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
     if constexpr (std::is_same<T, float>::value) {
+        if (a.tma.ntiles > 0 && R == 3 && mode == KRON_CHEB && a.b == 32 && a.ldx == 32 && !a.chunk && !a.sched)
+            return launch_kron_tma(a, s);
         if (v4_ok(a) && !a.chunk) {
             if (R == 3) {
                 switch (mode) {

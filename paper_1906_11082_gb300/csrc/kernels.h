@@ -12,6 +12,29 @@ uint64_t launches_so_far();
 
 enum KronMode { KRON_PLAIN = 0, KRON_CHEB = 1, KRON_CHEB_FILT = 2, KRON_CORI = 3 };
 
+// Row tiles of a scalar CSR matrix for the bulk-copy staged mass step
+// (mass_tma.cu): tile t covers rows [r0, r1) (at most kTmaRows rows, at
+// most kTmaDcap distinct neighbour nodes, at most kTmaEcap stored
+// entries); its distinct neighbour nodes are ucol[u0 .. u0 + nu) and
+// lcol[e] is the position of entry e's column in that list. vals, rowptr,
+// dinv are padded copies of the float matrix (so that 16-byte windows
+// never leave the allocation); ldiag[i] is the position of row i's own
+// node in its tile's list. err: a device flag a timed-out wait sets.
+constexpr int kTmaRows = 32;
+constexpr int kTmaDcap = 192;
+constexpr int kTmaEcap = 1024;
+struct TmaTiles {
+    int ntiles = 0;
+    const int4* desc = nullptr;     // (r0, r1, u0, nu) per tile
+    const int* ucol = nullptr;
+    const uint16_t* lcol = nullptr;
+    const float* vals = nullptr;
+    const int* rowptr = nullptr;
+    const float* dinv = nullptr;
+    const uint16_t* ldiag = nullptr;
+    int* err = nullptr;
+};
+
 // Y (or the Chebyshev / filter epilogue) from the scalar CSR matrix A
 // applied as A (x) I_R to row-major blocks of b columns. A node row i owns
 // the R consecutive rows R*i .. R*i+R-1 of every block.
@@ -58,7 +81,17 @@ struct KronArgs {
     int vec = 1;
     int vec_threads = 32;    // CTA size of the vectorised kernel, R = 3 (32 .. 1024, power of two)
     int vec_threads_p = 128; // the same for R = 1
+    // bulk-copy staged tiles (R = 3, float, b = ldx = 32, CHEB): ntiles > 0 selects mass_tma.cu
+    TmaTiles tma;
 };
+
+// The staged float mass step (one Chebyshev semi-iteration step of
+// M_rho (x) I_3 on 32 columns): persistent CTAs, one producer warp filling
+// two shared-memory stages by cp.async.bulk, eight consumer warps.
+int launch_kron_tma(const KronArgs<float>& a, cudaStream_t s);
+// Host check of the device flag of a staged kernel (synchronises stream s):
+// NM_OK, or NM_ETIMEOUT if a bounded wait of a launch ran out.
+int tma_status(int* err_dev, cudaStream_t s);
 
 template <typename T>
 int launch_kron(int R, int mode, const KronArgs<T>& a, cudaStream_t s);

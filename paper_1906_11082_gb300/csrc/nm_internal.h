@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/nm.h"
+#include "kernels.h"
 
 namespace nm {
 
@@ -88,7 +89,14 @@ struct DevCSR {
     DevBuf tile_uptr;  // int32 [ntiles + 1]
     DevBuf tile_ucol;  // int32
     DevBuf lcol;       // uint16 [nnz]
+    // row tiles of the bulk-copy staged float mass step (mass_tma.cu),
+    // built on first use: state 0 not built, 1 built, -1 not eligible
+    int tma_state = 0;
+    TmaTiles tma;
+    DevBuf tma_desc, tma_ucol, tma_lcol, tma_vals, tma_rowptr, tma_dinv, tma_ldiag, tma_err;
 };
+
+int build_tma_tiles(DevCSR& A, cudaStream_t s);
 
 struct Workspace {
     DevBuf buf;      // filter recurrence scratch
@@ -140,6 +148,7 @@ struct nm_problem {
     // SM-local persistent schedule of the semi-iteration kernels
     int use_sched = 0;
     int use_vec = 1;      // vectorised gathers for float b = 32 blocks
+    int use_tma = 1;      // bulk-copy staged tiles for the float b = 32 mass steps
     int vec_threads = 32;   // their CTA size (3-component rows)
     int vec_threads_p = 128;  // ... and for the 1-component pressure rows
     int df_threads = 32;    // CTA size of the lane-group double-float kernels

@@ -423,6 +423,7 @@ static int cheb32(nm_problem* P, const DevCSR& A, int R, int b, int k, double lo
         a.ldn = b;
         a.om = (float)om;
         a.inv_theta = (float)cc.inv_theta;
+        if (R == 3 && b == 32 && P->use_tma && A.tma_state == 1) a.tma = A.tma;
         NM_TRY(launch_kron<float>(R, KRON_CHEB, a, s));
     }
     if (R == 3) NM_TRY(prof_end(P, s, 2, ev, k - 1));
@@ -573,6 +574,7 @@ static int filter_apply_mixed(nm_problem* P, const nm_filter* f, const double* Y
     if (f->m_lo > 0 || f->m_hi > 0) return fail(NM_EUNSUPPORTED, "mixed mode uses the P2 element bounds");
     NM_TRY(ensure_f32(P, s));
     if (P->use_df) NM_TRY(ensure_df(P, s));
+    if (b == 32 && P->use_tma) NM_TRY(build_tma_tiles(P->Mr, s));
     const int64_t n = P->info.n;
     MixScratch S;
     NM_TRY(get_mix_scratch(P, b, S));
@@ -724,6 +726,7 @@ int solve_M_mixed_pub(nm_problem* P, int k_M, const double* W, int64_t ldw, doub
                       cudaStream_t s) {
     NM_TRY(ensure_f32(P, s));
     if (P->use_df) NM_TRY(ensure_df(P, s));
+    if (b == 32 && P->use_tma) NM_TRY(build_tma_tiles(P->Mr, s));
     MixScratch S;
     NM_TRY(get_mix_scratch(P, b, S));
     NM_TRY(mixed_solve(P, P->Mr, 3, b, k_M, W, ldw, S, P->use_df != 0, s));
@@ -1537,6 +1540,7 @@ int lanczos_step(nm_lanczos* L, int* active_out) {
                         L->Wcat.as<double>(), B, &table, L->fin, L->fout, s));
     NM_CUDA(cudaStreamSynchronize(s));
     L->t_filter += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (P->Mr.tma_state == 1) NM_TRY(tma_status(P->Mr.tma.err, s));
     for (int g = 0; g < Sa; ++g) {
         SliceState& z = L->st[act[g]];
         double* W = L->Wcat.as<double>() + g * b;   // ld B

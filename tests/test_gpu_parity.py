@@ -669,3 +669,66 @@ def test_lanczos_begin_reuses_bounds(nm, ball):
     r3.step()
     c = r3.finish(allow_unconverged=True)[0]
     assert c.info["lam_hi"] == pytest.approx(a.info["lam_hi"], rel=1e-10)
+
+
+# ------------------------------------------------------------------ staged (bulk-copy) float mass step
+@pytest.mark.parametrize("k", [2, 3, 20])
+def test_tma_mass_step_matches_vectorised_kernel(nm, planet, k):
+    """The bulk-copy staged mass-step kernel (b = 32 float, the default)
+    computes the same float semi-iteration as the lane-group kernel: the
+    refined mixed solve agrees to float rounding of the sums (different
+    order), and with the oracle's refined solve at 1e-9."""
+    mesh, model, S, P = planet
+    Wc = np.random.default_rng(31).standard_normal((S.n, 32))
+    W = _dev(to_internal(P, Wc))
+    out = {}
+    for tma in (0, 1):
+        P.set_option("tma", tma)
+        X = torch.empty((S.n, 32), dtype=torch.float64, device=DEV)
+        P.solve_M(W, X, k_M=k, prec=nm.NM_MIXED)
+        out[tma] = _host(X)
+    P.set_option("tma", 1)
+    assert rel_err(out[1], out[0]) <= 2e-6
+    ref = filtlan.refined_solve(S.M, 1.0 / S.M.diagonal(), Wc, k)
+    assert rel_err(to_canonical(P, out[1]), ref) <= (1e-9 if k == 20 else 1e-5)
+
+
+def test_tma_filter_matches_oracle_and_reports_no_timeout(nm, planet):
+    """A whole mixed filter application on 32 columns with the staged
+    kernel matches the oracle's refined filter, and a Lanczos step after it
+    reads a clear time-out flag."""
+    mesh, model, S, P = planet
+    op = filtlan.Operator(S, k_M=20, k_P=20, refine=True)
+    lo, hi = filtlan.spectrum_bounds(op, S.n, steps=30, seed=1)
+    g, c, e = filtlan.filter_coeffs(lo, hi, 10.0, 40.0, 12)
+    Yc = np.random.default_rng(32).standard_normal((S.n, 32))
+    Z = torch.empty((S.n, 32), dtype=torch.float64, device=DEV)
+    P.set_option("tma", 1)
+    P.filter_apply(g, c, e, 20, _dev(to_internal(P, Yc)), Z, k_P=20, prec=nm.NM_MIXED)
+    ref = filtlan.filter_apply(op, g, c, e, Yc)
+    assert rel_err(to_canonical(P, _host(Z)), ref) <= 1e-8
+    P.set_interval(3.0, 6.0)
+    run = P.lanczos_begin(None, block=32, degree=20, k_M=20, k_P=20, max_blocks=3, seed=3, prec=nm.NM_MIXED)
+    run.step()
+    run.free()
+
+
+def test_tma_mass_step_many_tiles_per_cta(nm, ctx):
+    """On a mesh with ~20 tiles per CTA (every stage reused many times, the
+    producer waiting on released stages) the staged kernel agrees with the
+    lane-group kernel and with the oracle's refined solve."""
+    mesh, model = layered_planet(h=0.1, seed=7)
+    P = nm.Problem(ctx, mesh, model)
+    S = fem.assemble(mesh, model)
+    Wc = np.random.default_rng(33).standard_normal((S.n, 32))
+    W = _dev(to_internal(P, Wc))
+    out = {}
+    for tma in (0, 1):
+        P.set_option("tma", tma)
+        X = torch.empty((S.n, 32), dtype=torch.float64, device=DEV)
+        P.solve_M(W, X, k_M=20, prec=nm.NM_MIXED)
+        out[tma] = _host(X)
+    assert rel_err(out[1], out[0]) <= 2e-6
+    ref = filtlan.refined_solve(S.M, 1.0 / S.M.diagonal(), Wc, 20)
+    assert rel_err(to_canonical(P, out[1]), ref) <= 1e-9
+    P.free()
