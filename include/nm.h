@@ -213,14 +213,22 @@ int nm_problem_export(const nm_problem* prob, int which, int64_t* nrows, int64_t
  * SpMMs (the K_eff block SpMM and the refinement residuals) as
  * double-float arithmetic on the float units (values split exactly into
  * two floats, error-free products and sums, ~2^-48 relative); 0 runs them
- * in double. NM_EINVAL for an unknown key or value. */
+ * in double. key "tma": 1 runs the float mass steps of 32-column blocks
+ * (ld 32) as the shared-memory staged kernel: persistent CTAs whose
+ * producer warps copy each row tile's distinct neighbour records into a
+ * three-stage shared-memory ring (cp.async, with cp.async.bulk for the
+ * tile's index and value windows, completion on mbarriers) while consumer
+ * warps compute the previous tiles; the tiles (at most 32 rows and 160
+ * distinct neighbours) are built on the host on first use. Its waits are
+ * bounded: a wait that runs out makes the next nm_lanczos_step return
+ * NM_ETIMEOUT. 0 (default) uses the lane-group kernel. NM_EINVAL for an
+ * unknown key or value. */
 int nm_set_option(nm_problem* prob, const char* key, int64_t value);
 
 /* Autotuner: times one degree of the filter recurrence (precision prec,
  * block width b, inner steps k_M) on this problem for every kernel variant
  * of the options above ("sched", "chunk", "vec", "tile_rows"/"tile_kernel", and for
- * NM_MIXED "graphs" and
- * NM_MIXED "double_float"), keeps the fastest, and reports the time per
+ * NM_MIXED "graphs", "tma" and "double_float"), keeps the fastest, and reports the time per
  * column and degree of block widths 16, 32 and 64 with it. All variants
  * compute the same sums (up to rounding order). report: caller buffer
  * (may be NULL) for a one-line JSON summary, truncated to report_len. */
@@ -376,6 +384,30 @@ int nm_lanczos_free(nm_lanczos* run);
  * the interval (unit omega). */
 int nm_ritz(nm_problem* prob, nm_ritz_mode mode, const double* V, int64_t ldv, int m,
             const double* lam_e, nm_result** out);
+
+/* ---- dense products -------------------------------------------------------
+ * The dense algebra of the block Lanczos and the Ritz projections (Sec. 6.2:
+ * the Gram-Schmidt coefficients V^T M W and updates W - V C; Rayleigh-Ritz
+ * V^T K V, V^T M V and X = V S; Sec. 7: X^T R X) in FP64 accuracy on the
+ * tensor cores: each operand is cut into eight exact 7-bit pieces per
+ * chunk of 64 contraction terms (scaled to the largest entry of its row or
+ * column in the chunk), the 36 leading piece products run as bf16 tensor-
+ * core products with exact float accumulation, and the chunk sums are
+ * added in FP64. The error is of the order of 2^-53 times the sum over the
+ * contraction of the products of each row's and column's largest entries.
+ * Deterministic (fixed split and summation order). All pointers device.
+ * nm_gemm_tn: C (I x J, column-major, ld ldc) = alpha X^T Y + beta C with
+ *   X (K x I) and Y (K x J) row-major (ld ldx, ldy); the split parts of the
+ *   contraction use a workspace the context owns (grown on demand).
+ * nm_gemm_nn: D (I x J, row-major, ld ldd) = alpha X Y + beta D with X
+ *   (I x K) row-major (ld ldx) and Y (K x J) column-major (ld ldy).
+ * beta = 0 does not read C / D. NM_EINVAL for negative sizes or leading
+ * dimensions too small. Problems use these products unless the option
+ * "dense_tc" of nm_set_option is 0 (cuBLAS DGEMM then). */
+int nm_gemm_tn(nm_ctx* ctx, int64_t I, int64_t J, int64_t K, double alpha, const double* X, int64_t ldx,
+               const double* Y, int64_t ldy, double beta, double* C, int64_t ldc, void* stream);
+int nm_gemm_nn(nm_ctx* ctx, int64_t I, int64_t J, int64_t K, double alpha, const double* X, int64_t ldx,
+               const double* Y, int64_t ldy, double beta, double* D, int64_t ldd, void* stream);
 
 /* ---- kernel timing --------------------------------------------------------
  * With profiling enabled, every filter degree brackets its launch

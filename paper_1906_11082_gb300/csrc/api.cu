@@ -226,6 +226,11 @@ int nm_set_option(nm_problem* P, const char* key, int64_t value) {
         P->use_sched = (int)value;
         return NM_OK;
     }
+    if (std::string(key) == "dense_tc") {
+        if (value != 0 && value != 1) return fail(NM_EINVAL, "dense_tc must be 0 or 1");
+        P->ctx->dense_tc = (int)value;
+        return NM_OK;
+    }
     if (std::string(key) == "tma") {
         if (value != 0 && value != 1) return fail(NM_EINVAL, "tma must be 0 or 1");
         P->use_tma = (int)value;
@@ -487,6 +492,28 @@ int nm_ritz(nm_problem* P, nm_ritz_mode mode, const double* V, int64_t ldv, int 
     CtxScope sc(P->ctx);
     *out = nullptr;
     return ritz(P, mode, V, ldv, m, lam_e, out);
+}
+
+int nm_gemm_tn(nm_ctx* ctx, int64_t I, int64_t J, int64_t K, double alpha, const double* X, int64_t ldx,
+               const double* Y, int64_t ldy, double beta, double* C, int64_t ldc, void* stream) {
+    if (!ctx) return fail(NM_EINVAL, "null context");
+    CtxScope sc(ctx);
+    if (I < 0 || J < 0 || K < 0) return fail(NM_EINVAL, "negative size");
+    if (I == 0 || J == 0) return NM_OK;
+    if (!C || ldc < I || (K > 0 && (!X || !Y || ldx < I || ldy < J)))
+        return fail(NM_EINVAL, "null operand or leading dimension too small");
+    return ozaki_gemm_tn(ctx, (cudaStream_t)stream, I, J, K, alpha, X, ldx, Y, ldy, beta, C, ldc);
+}
+
+int nm_gemm_nn(nm_ctx* ctx, int64_t I, int64_t J, int64_t K, double alpha, const double* X, int64_t ldx,
+               const double* Y, int64_t ldy, double beta, double* D, int64_t ldd, void* stream) {
+    if (!ctx) return fail(NM_EINVAL, "null context");
+    CtxScope sc(ctx);
+    if (I < 0 || J < 0 || K < 0) return fail(NM_EINVAL, "negative size");
+    if (I == 0 || J == 0) return NM_OK;
+    if (!D || ldd < J || (K > 0 && (!X || !Y || ldx < K || ldy < K)))
+        return fail(NM_EINVAL, "null operand or leading dimension too small");
+    return ozaki_gemm_nn((cudaStream_t)stream, I, J, K, alpha, X, ldx, Y, ldy, beta, D, ldd);
 }
 
 int nm_profile(nm_problem* P, int enable, int reset) {

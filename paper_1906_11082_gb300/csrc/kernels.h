@@ -21,7 +21,7 @@ enum KronMode { KRON_PLAIN = 0, KRON_CHEB = 1, KRON_CHEB_FILT = 2, KRON_CORI = 3
 // never leave the allocation); ldiag[i] is the position of row i's own
 // node in its tile's list. err: a device flag a timed-out wait sets.
 constexpr int kTmaRows = 32;
-constexpr int kTmaDcap = 192;
+constexpr int kTmaDcap = 160;
 constexpr int kTmaEcap = 1024;
 struct TmaTiles {
     int ntiles = 0;

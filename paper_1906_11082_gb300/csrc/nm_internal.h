@@ -111,7 +111,19 @@ struct nm_ctx {
     cublasHandle_t cublas = nullptr;
     cusolverDnHandle_t cusolver = nullptr;
     cudaStream_t stream = nullptr;   // library-owned stream for blocking calls
+    nm::DevBuf gemm_ws;              // split parts of the tensor-core dense products
+    int dense_tc = 1;                // dense products on the tensor cores (0: cuBLAS DGEMM)
 };
+
+namespace nm {
+// FP64-accurate dense products on the tensor cores (ozaki_gemm.cu).
+// TN: C (I x J, col-major, ldc) = alpha X^T Y + beta C, X: K x I, Y: K x J row-major.
+int ozaki_gemm_tn(nm_ctx* ctx, cudaStream_t s, int64_t I, int64_t J, int64_t K, double alpha, const double* X,
+                  int64_t ldx, const double* Y, int64_t ldy, double beta, double* C, int64_t ldc);
+// NN: D (I x J, row-major, ldd) = alpha X Y + beta D, X: I x K row-major, Y: K x J col-major.
+int ozaki_gemm_nn(cudaStream_t s, int64_t I, int64_t J, int64_t K, double alpha, const double* X, int64_t ldx,
+                  const double* Y, int64_t ldy, double beta, double* D, int64_t ldd);
+}  // namespace nm
 
 struct nm_problem {
     nm_ctx* ctx = nullptr;
@@ -148,7 +160,7 @@ struct nm_problem {
     // SM-local persistent schedule of the semi-iteration kernels
     int use_sched = 0;
     int use_vec = 1;      // vectorised gathers for float b = 32 blocks
-    int use_tma = 1;      // bulk-copy staged tiles for the float b = 32 mass steps
+    int use_tma = 0;      // shared-memory staged tiles for the float b = 32 mass steps (option "tma")
     int vec_threads = 32;   // their CTA size (3-component rows)
     int vec_threads_p = 128;  // ... and for the 1-component pressure rows
     int df_threads = 32;    // CTA size of the lane-group double-float kernels

@@ -981,19 +981,20 @@ int autotune(nm_problem* P, int b, nm_prec prec, int k_M, std::string* report) {
     } else {
         NM_TRY(launch_philox_normal(n * 64, 7, Y.as<double>(), s));
     }
-    struct Cfg { int sched, tile, tk, df, chunk, vec, graphs; };
+    struct Cfg { int sched, tile, tk, df, chunk, vec, graphs, tma; };
     std::vector<Cfg> cfgs;
     const int df1 = prec == NM_MIXED ? 1 : P->use_df;
     for (int sched : {0, 1})
         for (int df : (prec == NM_MIXED ? std::vector<int>{1, 0} : std::vector<int>{P->use_df}))
-            cfgs.push_back({sched, 0, 2, df, 0, 1, 0});
-    if (prec == NM_MIXED) cfgs.push_back({0, 0, 2, 1, 0, 1, 1});
-    if (prec != NM_F64 && b == 32) cfgs.push_back({0, 0, 2, df1, 0, 0, 0});
+            cfgs.push_back({sched, 0, 2, df, 0, 1, 0, 0});
+    if (prec == NM_MIXED) cfgs.push_back({0, 0, 2, 1, 0, 1, 1, 0});
+    if (prec == NM_MIXED && b == 32) cfgs.push_back({0, 0, 2, 1, 0, 1, 0, 1});
+    if (prec != NM_F64 && b == 32) cfgs.push_back({0, 0, 2, df1, 0, 0, 0, 0});
     if (b >= 17)
-        for (int ch : {256, 512, 1024}) cfgs.push_back({0, 0, 2, df1, ch, 0, 0});
+        for (int ch : {256, 512, 1024}) cfgs.push_back({0, 0, 2, df1, ch, 0, 0, 0});
     if (prec != NM_F64 && b == 32) {
-        cfgs.push_back({0, 16, 2, df1, 0, 0, 0});
-        cfgs.push_back({0, 32, 2, df1, 0, 0, 0});
+        cfgs.push_back({0, 16, 2, df1, 0, 0, 0, 0});
+        cfgs.push_back({0, 32, 2, df1, 0, 0, 0, 0});
     }
     const int reps = 6;   // degrees per timing (graph replay needs at least 3)
     double best = 1e300;
@@ -1006,16 +1007,17 @@ int autotune(nm_problem* P, int b, nm_prec prec, int k_M, std::string* report) {
         P->use_chunk = c.chunk;
         P->use_vec = c.vec;
         P->use_graphs = c.graphs;
+        P->use_tma = c.tma;
         NM_TRY(set_tile_rows(P, c.tile));
         if (c.tile) P->Mr.tile_kernel = P->Pn.tile_kernel = c.tk;
         double ms = 0;
         NM_TRY(time_degree(P, b, prec, k_M, Y.p, Z.p, reps, &ms));
         ms /= reps;
-        char buf[160];
+        char buf[192];
         snprintf(buf, sizeof buf,
-                 "%s{\"sched\": %d, \"chunk\": %d, \"vec\": %d, \"graphs\": %d, \"tile_rows\": %d, "
+                 "%s{\"sched\": %d, \"chunk\": %d, \"vec\": %d, \"graphs\": %d, \"tma\": %d, \"tile_rows\": %d, "
                  "\"double_float\": %d, \"ms_per_degree\": %.4f}",
-                 i ? ", " : "", c.sched, c.chunk, c.vec, c.graphs, c.tile, c.df, ms);
+                 i ? ", " : "", c.sched, c.chunk, c.vec, c.graphs, c.tma, c.tile, c.df, ms);
         rep += buf;
         if (ms < best) {
             best = ms;
@@ -1027,11 +1029,12 @@ int autotune(nm_problem* P, int b, nm_prec prec, int k_M, std::string* report) {
     P->use_chunk = bestc.chunk;
     P->use_vec = bestc.vec;
     P->use_graphs = bestc.graphs;
+    P->use_tma = bestc.tma;
     NM_TRY(set_tile_rows(P, bestc.tile));
     if (bestc.tile) P->Mr.tile_kernel = P->Pn.tile_kernel = bestc.tk;
     rep += "], \"chosen\": {\"sched\": " + std::to_string(bestc.sched) + ", \"chunk\": " +
            std::to_string(bestc.chunk) + ", \"vec\": " + std::to_string(bestc.vec) + ", \"graphs\": " +
-           std::to_string(bestc.graphs) + ", \"tile_rows\": " +
+           std::to_string(bestc.graphs) + ", \"tma\": " + std::to_string(bestc.tma) + ", \"tile_rows\": " +
            std::to_string(bestc.tile) + ", \"double_float\": " + std::to_string(bestc.df) + "}, \"us_per_column_degree\": {";
     int first = 1;
     for (int bb : {16, 32, 64}) {
@@ -1084,9 +1087,12 @@ struct Dense {
     cudaStream_t s;
 };
 
-// C (m x b, col-major) = V^T (M W): V row-major n x m (ld ldv), MW row-major n x b (ld b)
+// C (m x b, col-major) = V^T (M W) + beta C: V row-major n x m (ld ldv),
+// MW row-major n x b (ld ldw). By default the FP64-accurate tensor-core
+// product (ozaki_gemm.cu); option "dense_tc" = 0 uses cuBLAS DGEMM.
 static int gemm_VtW(nm_ctx* ctx, int64_t n, int m, int b, const double* V, int64_t ldv,
                     const double* MW, int64_t ldw, double* C, double beta) {
+    if (ctx->dense_tc) return ozaki_gemm_tn(ctx, ctx->stream, m, b, n, 1.0, V, ldv, MW, ldw, beta, C, m);
     const double one = 1.0;
     NM_CUBLAS(cublasDgemm(ctx->cublas, CUBLAS_OP_N, CUBLAS_OP_T, m, b, (int)n, &one, V, (int)ldv, MW,
                           (int)ldw, &beta, C, m));
@@ -1096,9 +1102,21 @@ static int gemm_VtW(nm_ctx* ctx, int64_t n, int m, int b, const double* V, int64
 // W (row-major n x b, ld ldw) += alpha * V C, C col-major m x b
 static int gemm_WmVC(nm_ctx* ctx, int64_t n, int m, int b, double alpha, const double* V, int64_t ldv,
                      const double* C, int ldc, double* W, int64_t ldw) {
+    if (ctx->dense_tc) return ozaki_gemm_nn(ctx->stream, n, b, m, alpha, V, ldv, C, ldc, 1.0, W, ldw);
     const double one = 1.0;
     NM_CUBLAS(cublasDgemm(ctx->cublas, CUBLAS_OP_T, CUBLAS_OP_N, b, (int)n, m, &alpha, C, ldc, V,
                           (int)ldv, &one, W, (int)ldw));
+    return NM_OK;
+}
+
+// X (row-major n x k, ld ldx) = V S with V row-major n x m (ld ldv) and S
+// col-major m x k (ld lds).
+static int gemm_VS(nm_ctx* ctx, int64_t n, int m, int k, const double* V, int64_t ldv, const double* S, int lds,
+                   double* X, int64_t ldx) {
+    if (ctx->dense_tc) return ozaki_gemm_nn(ctx->stream, n, k, m, 1.0, V, ldv, S, lds, 0.0, X, ldx);
+    const double one = 1.0, zero = 0.0;
+    NM_CUBLAS(cublasDgemm(ctx->cublas, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)n, m, &one, S, lds, V, (int)ldv, &zero, X,
+                          (int)ldx));
     return NM_OK;
 }
 
@@ -1266,12 +1284,9 @@ static int rayleigh_ritz(nm_problem* P, const double* V, int64_t ldv, int m, dou
     NM_TRY(lam_d.alloc(k * sizeof(double)));
     NM_TRY(nr.alloc(k * sizeof(double)));
     NM_TRY(nm_.alloc(k * sizeof(double)));
-    const double one = 1.0, zero = 0.0;
-    // Xc (k x n) = S_sel^T Vc
+    // X (n x k) = V S_sel
     auto proj = [&](const double* Vsrc, int64_t ld, double* dst) -> int {
-        NM_CUBLAS(cublasDgemm(ctx->cublas, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)n, m, &one, Ssel, m, Vsrc, (int)ld,
-                              &zero, dst, k));
-        return NM_OK;
+        return gemm_VS(ctx, n, m, k, Vsrc, ld, Ssel, m, dst, k);
     };
     NM_TRY(proj(KV.as<double>(), m, KX.as<double>()));
     NM_TRY(proj(MV.as<double>(), m, MX.as<double>()));
@@ -1818,11 +1833,8 @@ int ritz(nm_problem* P, nm_ritz_mode mode, const double* V, int64_t ldv, int m, 
             NM_TRY(Ui.alloc((size_t)n * k * sizeof(double)));
             NM_CUDA(cudaMemcpy(yrd.p, yr.data(), yr.size() * sizeof(double), cudaMemcpyHostToDevice));
             NM_CUDA(cudaMemcpy(yid.p, yi.data(), yi.size() * sizeof(double), cudaMemcpyHostToDevice));
-            const double one = 1.0, zero = 0.0;
-            NM_CUBLAS(cublasDgemm(ctx->cublas, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)n, m, &one, yrd.as<double>(), m, V,
-                                  (int)ldv, &zero, Ur.as<double>(), k));
-            NM_CUBLAS(cublasDgemm(ctx->cublas, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)n, m, &one, yid.as<double>(), m, V,
-                                  (int)ldv, &zero, Ui.as<double>(), k));
+            NM_TRY(gemm_VS(ctx, n, m, k, V, ldv, yrd.as<double>(), m, Ur.as<double>(), k));
+            NM_TRY(gemm_VS(ctx, n, m, k, V, ldv, yid.as<double>(), m, Ui.as<double>(), k));
             // full quadratic residual ||w^2 M u - 2 i w R u - K u|| / ||w^2 M u|| (reported, not gated)
             DevBuf KUr, KUi, MUr, MUi, RUr, RUi;
             for (DevBuf* d : {&KUr, &KUi, &MUr, &MUi, &RUr, &RUi}) NM_TRY(d->alloc((size_t)n * k * sizeof(double)));

@@ -31,7 +31,7 @@ EXPORTS = (
     "nm_result_get_info", "nm_result_values", "nm_result_vectors", "nm_result_free",
     "nm_profile", "nm_profile_read", "nm_kernel_launches", "nm_set_option", "nm_autotune",
     "nm_lanczos_multi", "nm_filter_apply_static", "nm_lanczos_begin", "nm_lanczos_step",
-    "nm_lanczos_get_info", "nm_lanczos_finish", "nm_lanczos_free",
+    "nm_lanczos_get_info", "nm_lanczos_finish", "nm_lanczos_free", "nm_gemm_tn", "nm_gemm_nn",
 )
 
 
@@ -122,6 +122,8 @@ def _load():
         "nm_lanczos_get_info": [vp, i32, C.POINTER(nm_lanczos_info)],
         "nm_lanczos_finish": [vp, vp],
         "nm_lanczos_free": [vp],
+        "nm_gemm_tn": [vp, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp],
+        "nm_gemm_nn": [vp, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -195,6 +197,22 @@ class Context:
 
     def _adopt(self, obj):
         self._children.add(obj)
+
+    def gemm_tn(self, X, Y, C, alpha=1.0, beta=0.0, stream=None):
+        """C (I x J, column-major: a torch tensor of shape (J, I)) = alpha X^T Y
+        + beta C for row-major float64 device tensors X (K x I), Y (K x J)."""
+        K, I = X.shape
+        J = Y.shape[1]
+        _check(_lib.nm_gemm_tn(self.h, I, J, K, alpha, _dptr(X), X.stride(0), _dptr(Y), Y.stride(0), beta, _dptr(C),
+                               C.stride(0), _stream(stream)), self.h)
+
+    def gemm_nn(self, X, Y, D, alpha=1.0, beta=0.0, stream=None):
+        """D (I x J, row-major) = alpha X Y + beta D for row-major X (I x K) and
+        column-major Y (K x J: a torch tensor of shape (J, K))."""
+        I, K = X.shape
+        J = Y.shape[0]
+        _check(_lib.nm_gemm_nn(self.h, I, J, K, alpha, _dptr(X), X.stride(0), _dptr(Y), Y.stride(0), beta, _dptr(D),
+                               D.stride(0), _stream(stream)), self.h)
 
     def close(self):
         if self.h:
@@ -440,7 +458,7 @@ class Problem:
     def autotune(self, b=32, prec=None, k_M=0):
         """Pick the fastest kernel variant for this problem; returns the report."""
         import json
-        buf = C.create_string_buffer(4096)
+        buf = C.create_string_buffer(16384)
         _check(_lib.nm_autotune(self.h, b, NM_MIXED if prec is None else prec, k_M, buf, len(buf)), self.ctx.h)
         return json.loads(buf.value.decode())
 

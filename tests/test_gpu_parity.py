@@ -671,10 +671,10 @@ def test_lanczos_begin_reuses_bounds(nm, ball):
     assert c.info["lam_hi"] == pytest.approx(a.info["lam_hi"], rel=1e-10)
 
 
-# ------------------------------------------------------------------ staged (bulk-copy) float mass step
+# ------------------------------------------------------------------ staged (shared-memory) float mass step
 @pytest.mark.parametrize("k", [2, 3, 20])
 def test_tma_mass_step_matches_vectorised_kernel(nm, planet, k):
-    """The bulk-copy staged mass-step kernel (b = 32 float, the default)
+    """The shared-memory staged mass-step kernel (option tma, b = 32 float)
     computes the same float semi-iteration as the lane-group kernel: the
     refined mixed solve agrees to float rounding of the sums (different
     order), and with the oracle's refined solve at 1e-9."""
@@ -687,7 +687,7 @@ def test_tma_mass_step_matches_vectorised_kernel(nm, planet, k):
         X = torch.empty((S.n, 32), dtype=torch.float64, device=DEV)
         P.solve_M(W, X, k_M=k, prec=nm.NM_MIXED)
         out[tma] = _host(X)
-    P.set_option("tma", 1)
+    P.set_option("tma", 0)
     assert rel_err(out[1], out[0]) <= 2e-6
     ref = filtlan.refined_solve(S.M, 1.0 / S.M.diagonal(), Wc, k)
     assert rel_err(to_canonical(P, out[1]), ref) <= (1e-9 if k == 20 else 1e-5)
@@ -711,6 +711,7 @@ def test_tma_filter_matches_oracle_and_reports_no_timeout(nm, planet):
     run = P.lanczos_begin(None, block=32, degree=20, k_M=20, k_P=20, max_blocks=3, seed=3, prec=nm.NM_MIXED)
     run.step()
     run.free()
+    P.set_option("tma", 0)
 
 
 def test_tma_mass_step_many_tiles_per_cta(nm, ctx):
@@ -732,3 +733,84 @@ def test_tma_mass_step_many_tiles_per_cta(nm, ctx):
     ref = filtlan.refined_solve(S.M, 1.0 / S.M.diagonal(), Wc, 20)
     assert rel_err(to_canonical(P, out[1]), ref) <= 1e-9
     P.free()
+
+
+# ------------------------------------------------------------------ dense products on the tensor cores
+def _scaled(rng, rows, cols, spread=6.0):
+    """Gaussian entries with row and column scales over 10^(+-spread/2)
+    and a few exact zeros, negatives and tiny (subnormal-range) values."""
+    A = rng.standard_normal((rows, cols))
+    A *= 10.0 ** rng.uniform(-spread / 2, spread / 2, (rows, 1))
+    A *= 10.0 ** rng.uniform(-1, 1, (1, cols))
+    A[rng.random((rows, cols)) < 0.01] = 0.0
+    A[rng.random((rows, cols)) < 0.001] *= 1e-300
+    return A
+
+
+def _chunk_bound(Xk, Yk):
+    """2^-48 sum over 64-term chunks of the contraction of 64 max|X| max|Y|
+    per output entry: the splitting keeps each entry to 2^-52 of its row's
+    (column's) largest entry in the chunk and drops piece products below
+    2^-51 of the product of the two largest. Xk: K x I, Yk: K x J."""
+    K = Xk.shape[0]
+    out = np.zeros((Xk.shape[1], Yk.shape[1]))
+    for k0 in range(0, K, 64):
+        mx = np.abs(Xk[k0:k0 + 64]).max(axis=0)
+        my = np.abs(Yk[k0:k0 + 64]).max(axis=0)
+        out += 64.0 * np.outer(mx, my)
+    return 2.0 ** -48 * out + 1e-290
+
+
+@pytest.mark.parametrize("I,J,K", [(1, 1, 1), (70, 21, 1000), (64, 16, 64), (130, 33, 200003), (5, 40, 129)])
+def test_gemm_tn_fp64_accuracy(nm, ctx, I, J, K):
+    """C = alpha X^T Y + beta C (the Gram-Schmidt and Ritz projection shape)
+    against the FP64 product of numpy within the splitting's bound; identical
+    on a second call (deterministic split sums)."""
+    rng = np.random.default_rng(I * 7 + J * 13 + K)
+    X, Y = _scaled(rng, K, I), _scaled(rng, K, J)
+    C0 = rng.standard_normal((J, I))           # column-major I x J
+    alpha, beta = -1.5, 0.25
+    ref = alpha * (X.T @ Y) + beta * C0.T
+    Ct = _dev(C0)
+    ctx.gemm_tn(_dev(X), _dev(Y), Ct, alpha=alpha, beta=beta)
+    got = _host(Ct).T
+    err = np.abs(got - ref)
+    bound = abs(alpha) * _chunk_bound(X, Y) + 2.0 ** -50 * np.abs(beta * C0.T)
+    assert (err <= bound).all(), float((err / bound).max())
+    # and much tighter than a float product would be
+    assert err.max() <= 1e-12 * np.abs(ref).max()
+    Ct2 = _dev(C0)
+    ctx.gemm_tn(_dev(X), _dev(Y), Ct2, alpha=alpha, beta=beta)
+    assert torch.equal(Ct, Ct2)
+
+
+@pytest.mark.parametrize("I,J,K", [(1, 1, 1), (1000, 32, 576), (333, 7, 65), (64, 64, 64), (100003, 16, 96)])
+def test_gemm_nn_fp64_accuracy(nm, ctx, I, J, K):
+    """D = alpha X Y + beta D (the W - V C and X = V S shape) against numpy
+    FP64 within the splitting's bound."""
+    rng = np.random.default_rng(I + J * 3 + K * 5)
+    X = _scaled(rng, I, K)
+    Y = _scaled(rng, K, J)
+    D0 = rng.standard_normal((I, J))
+    for alpha, beta in ((1.0, 0.0), (-1.0, 1.0)):
+        ref = alpha * (X @ Y) + beta * D0
+        Dt = _dev(D0)
+        ctx.gemm_nn(_dev(X), _dev(np.ascontiguousarray(Y.T)), Dt, alpha=alpha, beta=beta)
+        err = np.abs(_host(Dt) - ref)
+        bound = _chunk_bound(X.T, Y) + 2.0 ** -50 * np.abs(beta * D0)
+        assert (err <= bound).all(), float((err / bound).max())
+
+
+def test_dense_tc_option_agrees_with_dgemm(nm, ball):
+    """A slice solved with the tensor-core products and with cuBLAS DGEMM
+    (option dense_tc) gives the same eigenvalues to 1e-12."""
+    w, S, P = ball
+    P.set_interval(0.0, 3.0)
+    kw = dict(block=8, degree=100, k_M=40, k_P=40, max_blocks=16, seed=5)
+    a = P.lanczos_slice(**kw)
+    P.set_option("dense_tc", 0)
+    b = P.lanczos_slice(**kw)
+    P.set_option("dense_tc", 1)
+    assert len(a.lam) == len(b.lam) == 16
+    lam_max = np.abs(a.lam).max()
+    assert np.allclose(a.lam, b.lam, rtol=1e-12, atol=1e-12 * lam_max)
