@@ -302,7 +302,11 @@ int nm_filter_apply(nm_problem* prob, const nm_filter* f, const void* Y, int64_t
  *    the recurrence). Calls whose kernels overlap on the GPU (different
  *    streams, threads, contexts or problems) race on it: serialise them.
  *  - The first call on a device looks up the array's device address with
- *    cudaGetSymbolAddress; make that first call before any stream capture.
+ *    cudaGetSymbolAddress and keeps it for the life of the process; make
+ *    that first call before any stream capture. The kept address does not
+ *    survive cudaDeviceReset (or any other end of the device's primary
+ *    context) in the same process: do not call this entry point on a
+ *    device after resetting it.
  *  - Not recorded by nm_profile. Other errors as nm_filter_apply. */
 #define NM_STATIC_SCRATCH_BYTES (16u << 20)
 int nm_filter_apply_static(nm_problem* prob, const nm_filter* f, const double* Y, int64_t ldy, double* Z,
@@ -317,7 +321,8 @@ int nm_lanczos_slice(nm_problem* prob, const nm_slice_opts* opts, nm_result** ou
 
 /* Batched slices: nslices slices (lo[i], hi[i] in the given unit, as in
  * nm_set_interval) solved in lockstep with one filter recurrence per block
- * step over the concatenated blocks (nslices * block <= 64 columns; the
+ * step over the concatenated blocks (up to 64 columns per recurrence: more
+ * slices are filtered in groups of 64 / block slices; the
  * slices share the spectrum bounds and the Chebyshev map, each keeps its
  * own coefficients, basis, reorthogonalisation, convergence test and
  * Rayleigh-Ritz). out: caller array of nslices result pointers.
@@ -348,11 +353,25 @@ int nm_lanczos_multi(nm_problem* prob, const nm_slice_opts* opts, int nslices, c
  *                     pencil; a slice whose Ritz pairs all pass tol stops.
  *                     *active = slices still running (0: call finish).
  *   nm_lanczos_get_info progress of slice i (host copy, no synchronisation).
- *   nm_lanczos_finish the results of every slice (out: caller array of
- *                     nslices pointers; a Rayleigh-Ritz on the current basis
- *                     of a slice that has none yet). NM_ENOTCONV if a slice
- *                     did not pass tol; the results are returned all the
- *                     same and belong to the caller (nm_result_free).
+ *   nm_lanczos_add    a slice joins the running batch (continuous batching):
+ *                     its filter on the run's spectrum bounds, degree and
+ *                     options, its start block (start: device n x block,
+ *                     ld block, read during this call; NULL: Philox from
+ *                     seed) and its Cholesky-QR; it takes block steps from
+ *                     the next nm_lanczos_step on, with its own block
+ *                     counter. *index = its slice number (slices are
+ *                     numbered in the order they were begun or added).
+ *   nm_lanczos_take   the result of one slice, which leaves the run (its
+ *                     basis is released); a slice still running is stopped
+ *                     with a Rayleigh-Ritz on its current basis and
+ *                     NM_ENOTCONV (the result is returned all the same).
+ *   nm_lanczos_finish the results of every slice not taken yet (out:
+ *                     caller array with one pointer per slice begun or
+ *                     added; taken slices get NULL; a Rayleigh-Ritz on the
+ *                     current basis of a slice that has none yet).
+ *                     NM_ENOTCONV if a slice did not pass tol; the results
+ *                     are returned all the same and belong to the caller
+ *                     (nm_result_free).
  *   nm_lanczos_free   releases the run (its bases); call after finish, or
  *                     instead of it to abandon the run.
  *
@@ -373,6 +392,9 @@ int nm_lanczos_begin(nm_problem* prob, const nm_slice_opts* opts, int nslices, c
                      nm_unit unit, nm_lanczos** out);
 int nm_lanczos_step(nm_lanczos* run, int* active);
 int nm_lanczos_get_info(const nm_lanczos* run, int slice, nm_lanczos_info* info);
+int nm_lanczos_add(nm_lanczos* run, double lo, double hi, nm_unit unit, uint64_t seed, const double* start,
+                   int* index);
+int nm_lanczos_take(nm_lanczos* run, int slice, nm_result** out);
 int nm_lanczos_finish(nm_lanczos* run, nm_result** out);
 int nm_lanczos_free(nm_lanczos* run);
 

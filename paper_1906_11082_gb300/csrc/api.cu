@@ -41,6 +41,8 @@ int lanczos_begin(nm_problem* P, const nm_slice_opts* o, int S, const double* la
 int lanczos_step(nm_lanczos* L, int* active_out);
 int lanczos_finish(nm_lanczos* L, nm_result** out);
 int lanczos_state(const nm_lanczos* L, int slice, nm_lanczos_info* out);
+int lanczos_take(nm_lanczos* L, int q, nm_result** out);
+int lanczos_add(nm_lanczos* L, double lam_lo, double lam_hi, uint64_t seed, const double* start, int* index);
 void lanczos_free(nm_lanczos* L);
 nm_ctx* lanczos_ctx(const nm_lanczos* L);
 int ritz(nm_problem* P, nm_ritz_mode mode, const double* V, int64_t ldv, int m, const double* lam_e,
@@ -478,6 +480,21 @@ int nm_lanczos_finish(nm_lanczos* L, nm_result** out) {
     if (!L || !out) return fail(NM_EINVAL, "null argument");
     CtxScope sc(lanczos_ctx(L));
     return lanczos_finish(L, out);
+}
+
+int nm_lanczos_add(nm_lanczos* L, double lo, double hi, nm_unit unit, uint64_t seed, const double* start,
+                   int* index) {
+    if (!L || !index) return fail(NM_EINVAL, "null argument");
+    CtxScope sc(lanczos_ctx(L));
+    std::vector<double> l, u;
+    NM_TRY(slice_lambda(1, &lo, &hi, unit, l, u));
+    return lanczos_add(L, l[0], u[0], seed, start, index);
+}
+
+int nm_lanczos_take(nm_lanczos* L, int slice, nm_result** out) {
+    if (!L || !out) return fail(NM_EINVAL, "null argument");
+    CtxScope sc(lanczos_ctx(L));
+    return lanczos_take(L, slice, out);
 }
 
 int nm_lanczos_free(nm_lanczos* L) {

@@ -10,6 +10,7 @@
 #include <memory>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <vector>
 
 #include "kernels.h"
@@ -1407,8 +1408,9 @@ struct SliceState {
     std::vector<double> gamma;
     DevBuf V, MW, C, H, G;
     std::vector<double> Tfull;
+    int j = 0;                    // block steps this slice has taken
     int blocks = 0, m_used = 0;
-    bool active = true, converged = false, ok = true;
+    bool active = true, converged = false, ok = true, taken = false;
     int nwanted = 0, nconv = 0;   // at the last block step
     RRResult rr;
     nm_result* R = nullptr;
@@ -1416,33 +1418,85 @@ struct SliceState {
 
 }  // namespace nm
 
-// A filtered block Lanczos run of S slices in lockstep (S = 1: one slice),
-// advanced one block step at a time. The slices share the spectrum bounds,
-// hence the Chebyshev map (c, e) and the recurrence; their current blocks
-// are filtered together as one block of S b columns with a per-slice gamma
-// in the accumulation. Each slice has its own M-orthonormal basis, two-pass
-// CGS, Cholesky-QR, projected matrix, convergence test and Rayleigh-Ritz,
-// and leaves the batch when done.
+// A filtered block Lanczos run of several slices in lockstep, advanced one
+// block step at a time. The slices share the spectrum bounds, hence the
+// Chebyshev map (c, e) and the recurrence; their current blocks are
+// filtered together as one block with a per-slice gamma in the
+// accumulation. Each slice has its own M-orthonormal basis, two-pass CGS,
+// Cholesky-QR, projected matrix, convergence test and Rayleigh-Ritz, its
+// own block counter, and leaves the batch when done; slices may join a
+// running batch (nm_lanczos_add) and leave it (nm_lanczos_take).
 struct nm_lanczos {
     nm_problem* P = nullptr;
     nm_slice_opts o{};
-    int S = 0, b = 0, d = 0, k_M = 0, k_P = 0, check = 1, mmax = 0, ldv = 0;
+    int b = 0, d = 0, k_M = 0, k_P = 0, check = 1, mmax = 0, ldv = 0;
     double tol = 1e-6, conv_T = 1e-8, blo = 0, bhi = 0, c = 0, e = 0;
-    std::vector<nm::SliceState> st;
+    std::deque<nm::SliceState> st;   // slices never move once added
     nm::DevBuf Ycat, Wcat, gtab, fin, fout;
+    int cols_cap = 0, gtab_cap = 0;  // columns and slices the concatenated buffers hold
     double t_filter = 0.0;
-    int j = 0;   // block steps taken
+    int j = 0;   // block steps taken by the run
     std::chrono::steady_clock::time_point t_start;
 };
 
 namespace nm {
+
+// Filter, start block and first Cholesky-QR of a slice joining run L.
+static int slice_init(nm_lanczos* L, SliceState& z, double lam_lo, double lam_hi, const double* start,
+                      uint64_t seed) {
+    nm_problem* P = L->P;
+    cudaStream_t s = P->ctx->stream;
+    const int64_t n = P->info.n;
+    const int b = L->b, d = L->d, ldv = L->ldv;
+    z.lam_lo = lam_lo <= 0 ? -1e-8 * L->bhi : lam_lo;
+    z.lam_hi = lam_hi;
+    z.gamma.resize(d + 1);
+    jackson_step_coeffs(L->blo, L->bhi, z.lam_lo, z.lam_hi, d, z.gamma.data(), &L->c, &L->e);
+    const double pa = cheb_sum(z.gamma, (z.lam_lo - L->c) / L->e), pb = cheb_sum(z.gamma, (z.lam_hi - L->c) / L->e);
+    z.tau = z.lam_lo > L->blo ? 0.8 * std::min(pa, pb) : 0.8 * pb;
+    NM_TRY(z.V.alloc((size_t)n * ldv * sizeof(double)));
+    NM_TRY(z.MW.alloc((size_t)n * b * sizeof(double)));
+    NM_TRY(z.C.alloc((size_t)ldv * b * sizeof(double)));
+    NM_TRY(z.H.alloc((size_t)ldv * b * sizeof(double)));
+    NM_TRY(z.G.alloc((size_t)b * b * sizeof(double)));
+    z.Tfull.assign((size_t)L->mmax * L->mmax, 0.0);
+    if (start) {
+        NM_TRY(launch_scale_copy<double>(n, b, 1.0, start, b, z.V.as<double>(), ldv, s));
+    } else {
+        NM_TRY(launch_philox_normal(n * b, seed, z.MW.as<double>(), s));
+        NM_TRY(launch_scale_copy<double>(n, b, 1.0, z.MW.as<double>(), b, z.V.as<double>(), ldv, s));
+    }
+    int ok = 1;
+    NM_TRY(m_orth(P, z.V.as<double>(), ldv, b, z.MW.as<double>(), z.G.as<double>(), &ok, s));
+    if (!ok) return fail(NM_ENOTCONV, "start block is rank deficient in the M inner product");
+    return NM_OK;
+}
+
+// Room in the concatenated buffers for `slices` slices of b columns.
+static int ensure_cat(nm_lanczos* L, int slices) {
+    const int64_t n = L->P->info.n;
+    if (slices * L->b > L->cols_cap) {
+        const int cols = slices * L->b;
+        L->Ycat.release();
+        L->Wcat.release();
+        NM_TRY(L->Ycat.alloc((size_t)n * cols * sizeof(double)));
+        NM_TRY(L->Wcat.alloc((size_t)n * cols * sizeof(double)));
+        L->cols_cap = cols;
+    }
+    if (slices > L->gtab_cap) {
+        L->gtab.release();
+        NM_TRY(L->gtab.alloc((size_t)(L->d + 1) * slices * sizeof(double)));
+        L->gtab_cap = slices;
+    }
+    return NM_OK;
+}
 
 int lanczos_begin(nm_problem* P, const nm_slice_opts* o, int S, const double* lam_lo_in, const double* lam_hi_in,
                   nm_lanczos** out) {
     *out = nullptr;
     const int b = o->block;
     if (S < 1) return fail(NM_EINVAL, "need at least one slice");
-    if (b < 1 || (int64_t)b * S > 64) return fail(NM_EINVAL, "slices x block must be in 1..64");
+    if (b < 1 || b > 64) return fail(NM_EINVAL, "block width must be in 1..64");
     if (o->degree < 1) return fail(NM_EINVAL, "degree must be >= 1");
     if (o->max_blocks < 2) return fail(NM_EINVAL, "max_blocks must be >= 2");
     for (int q = 0; q < S; ++q)
@@ -1454,7 +1508,6 @@ int lanczos_begin(nm_problem* P, const nm_slice_opts* o, int S, const double* la
     L->P = P;
     L->o = *o;
     L->o.start = nullptr;
-    L->S = S;
     L->b = b;
     L->d = o->degree;
     L->k_M = o->k_M > 0 ? o->k_M : 57;
@@ -1464,8 +1517,6 @@ int lanczos_begin(nm_problem* P, const nm_slice_opts* o, int S, const double* la
     L->conv_T = o->filter_prec == NM_F32 ? 1e-5 : 1e-8;
     L->mmax = b * o->max_blocks;
     L->ldv = L->mmax + b;
-    const int64_t n = P->info.n;
-    const int d = L->d, ldv = L->ldv;
     const int bsteps = o->bounds_steps > 0 ? o->bounds_steps : 40;
     const uint64_t bseed = o->seed + 1;
     // The bounds depend only on (steps, k_M, seed): a problem keeps the last
@@ -1477,51 +1528,31 @@ int lanczos_begin(nm_problem* P, const nm_slice_opts* o, int S, const double* la
     } else {
         NM_TRY(spectrum_bounds(P, bsteps, L->k_M, bseed, &L->blo, &L->bhi));
     }
-    L->st = std::vector<SliceState>(S);
-    for (int q = 0; q < S; ++q) {
-        SliceState& z = L->st[q];
-        z.lam_lo = lam_lo_in[q] <= 0 ? -1e-8 * L->bhi : lam_lo_in[q];
-        z.lam_hi = lam_hi_in[q];
-        z.gamma.resize(d + 1);
-        jackson_step_coeffs(L->blo, L->bhi, z.lam_lo, z.lam_hi, d, z.gamma.data(), &L->c, &L->e);
-        const double pa = cheb_sum(z.gamma, (z.lam_lo - L->c) / L->e),
-                     pb = cheb_sum(z.gamma, (z.lam_hi - L->c) / L->e);
-        z.tau = z.lam_lo > L->blo ? 0.8 * std::min(pa, pb) : 0.8 * pb;
-        NM_TRY(z.V.alloc((size_t)n * ldv * sizeof(double)));
-        NM_TRY(z.MW.alloc((size_t)n * b * sizeof(double)));
-        NM_TRY(z.C.alloc((size_t)ldv * b * sizeof(double)));
-        NM_TRY(z.H.alloc((size_t)ldv * b * sizeof(double)));
-        NM_TRY(z.G.alloc((size_t)b * b * sizeof(double)));
-        z.Tfull.assign((size_t)L->mmax * L->mmax, 0.0);
-        // start block: the caller's (same for every slice) or Philox with a per-slice stream
-        if (o->start) {
-            NM_TRY(launch_scale_copy<double>(n, b, 1.0, o->start, b, z.V.as<double>(), ldv, s));
-        } else {
-            NM_TRY(launch_philox_normal(n * b, o->seed + 0x9E3779B97F4A7C15ull * q, z.MW.as<double>(), s));
-            NM_TRY(launch_scale_copy<double>(n, b, 1.0, z.MW.as<double>(), b, z.V.as<double>(), ldv, s));
-        }
-        int ok = 1;
-        NM_TRY(m_orth(P, z.V.as<double>(), ldv, b, z.MW.as<double>(), z.G.as<double>(), &ok, s));
-        if (!ok) return fail(NM_ENOTCONV, "start block is rank deficient in the M inner product");
-    }
-    NM_TRY(L->Ycat.alloc((size_t)n * S * b * sizeof(double)));
-    NM_TRY(L->Wcat.alloc((size_t)n * S * b * sizeof(double)));
-    NM_TRY(L->gtab.alloc((size_t)(d + 1) * S * sizeof(double)));
+    L->st.resize(S);
+    for (int q = 0; q < S; ++q)
+        NM_TRY(slice_init(L.get(), L->st[q], lam_lo_in[q], lam_hi_in[q], o->start,
+                          o->seed + 0x9E3779B97F4A7C15ull * q));
+    NM_TRY(ensure_cat(L.get(), S));
     NM_CUDA(cudaStreamSynchronize(s));
     *out = L.release();
     return NM_OK;
 }
 
+static bool slice_running(const nm_lanczos* L, const SliceState& z) {
+    return z.active && !z.taken && z.j < L->o.max_blocks;
+}
+
 int lanczos_active(const nm_lanczos* L) {
     int a = 0;
-    for (const SliceState& z : L->st) a += z.active ? 1 : 0;
-    return L->j < L->o.max_blocks ? a : 0;
+    for (const SliceState& z : L->st) a += slice_running(L, z) ? 1 : 0;
+    return a;
 }
 
 // One block step of every active slice: filter the current blocks, CGS2
 // and Cholesky-QR of each slice's new block, its projected matrix, and,
-// every check_every blocks (or at max_blocks), the convergence test and the
-// Rayleigh-Ritz of the slices whose wanted Ritz values have converged.
+// every check_every blocks of the slice (or at max_blocks), the convergence
+// test and the Rayleigh-Ritz of the slices whose wanted Ritz values have
+// converged.
 int lanczos_step(nm_lanczos* L, int* active_out) {
     nm_problem* P = L->P;
     nm_ctx* ctx = P->ctx;
@@ -1529,162 +1560,213 @@ int lanczos_step(nm_lanczos* L, int* active_out) {
     const nm_slice_opts* o = &L->o;
     const int64_t n = P->info.n;
     const int b = L->b, d = L->d, ldv = L->ldv, mmax = L->mmax;
-    const int j = L->j;
-    if (lanczos_active(L) == 0) {
+    std::vector<int> act;
+    for (int q = 0; q < (int)L->st.size(); ++q)
+        if (slice_running(L, L->st[q])) act.push_back(q);
+    if (act.empty()) {
         *active_out = 0;
         return NM_OK;
     }
-    std::vector<int> act;
-    for (int q = 0; q < L->S; ++q)
-        if (L->st[q].active) act.push_back(q);
-    const int Sa = (int)act.size();
-    const int B = Sa * b;
-    const int m = (j + 1) * b;
-    // gamma table of the active slices and their concatenated current blocks
-    std::vector<double> gt((size_t)(d + 1) * Sa);
-    for (int g = 0; g < Sa; ++g) {
-        for (int k = 0; k <= d; ++k) gt[(size_t)k * Sa + g] = L->st[act[g]].gamma[k];
-        NM_TRY(launch_scale_copy<double>(n, b, 1.0, L->st[act[g]].V.as<double>() + (int64_t)j * b, ldv,
-                                         L->Ycat.as<double>() + g * b, B, s));
-    }
-    NM_CUDA(cudaMemcpyAsync(L->gtab.p, gt.data(), gt.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    NM_CUDA(cudaStreamSynchronize(s));
-    auto t0 = std::chrono::steady_clock::now();
-    GammaTable table{L->gtab.as<double>(), gt.data(), Sa, b};
-    NM_TRY(filter_block(P, o->filter_prec, d, L->c, L->e, L->k_M, L->k_P, L->Ycat.as<double>(), B,
-                        L->Wcat.as<double>(), B, &table, L->fin, L->fout, s));
-    NM_CUDA(cudaStreamSynchronize(s));
-    L->t_filter += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (P->Mr.tma_state == 1) NM_TRY(tma_status(P->Mr.tma.err, s));
-    for (int g = 0; g < Sa; ++g) {
-        SliceState& z = L->st[act[g]];
-        double* W = L->Wcat.as<double>() + g * b;   // ld B
-        // CGS2 against the slice's basis in the M inner product
-        NM_CUDA(cudaMemsetAsync(z.H.p, 0, (size_t)m * b * sizeof(double), s));
-        for (int pass = 0; pass < 2; ++pass) {
-            NM_TRY(apply_M_pub<double>(P, W, B, z.MW.as<double>(), b, b, KRON_PLAIN, nullptr, s));
-            NM_TRY(gemm_VtW(ctx, n, m, b, z.V.as<double>(), ldv, z.MW.as<double>(), b, z.C.as<double>(), 0.0));
-            NM_TRY(gemm_WmVC(ctx, n, m, b, -1.0, z.V.as<double>(), ldv, z.C.as<double>(), m, W, B));
-            const double one = 1.0;
-            NM_CUBLAS(cublasDaxpy(ctx->cublas, m * b, &one, z.C.as<double>(), 1, z.H.as<double>(), 1));
+    // the active slices' blocks are filtered together, at most 64 columns
+    // (one recurrence over the concatenated block) at a time
+    const int per = std::max(1, 64 / b);
+    NM_TRY(ensure_cat(L, std::min((int)act.size(), per)));
+    for (size_t g0 = 0; g0 < act.size(); g0 += per) {
+        const int Sa = (int)std::min<size_t>(per, act.size() - g0);
+        const int B = Sa * b;
+        // gamma table of the group's slices and their concatenated current blocks
+        std::vector<double> gt((size_t)(d + 1) * Sa);
+        for (int g = 0; g < Sa; ++g) {
+            const SliceState& z = L->st[act[g0 + g]];
+            for (int k = 0; k <= d; ++k) gt[(size_t)k * Sa + g] = z.gamma[k];
+            NM_TRY(launch_scale_copy<double>(n, b, 1.0, z.V.as<double>() + (int64_t)z.j * b, ldv,
+                                             L->Ycat.as<double>() + g * b, B, s));
         }
-        std::vector<double> hH((size_t)m * b);
-        NM_CUDA(cudaMemcpyAsync(hH.data(), z.H.p, hH.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-        double* Vn = z.V.as<double>() + (int64_t)(j + 1) * b;
-        NM_TRY(launch_scale_copy<double>(n, b, 1.0, W, B, Vn, ldv, s));
-        int ok = 1;
-        NM_TRY(m_orth(P, Vn, ldv, b, z.MW.as<double>(), z.G.as<double>(), &ok, s));
-        z.ok = ok != 0;
-        std::vector<double> hR((size_t)b * b);
-        NM_CUDA(cudaMemcpy(hR.data(), z.G.p, hR.size() * sizeof(double), cudaMemcpyDeviceToHost));
-        for (int cc = 0; cc < b; ++cc)
+        NM_CUDA(cudaMemcpyAsync(L->gtab.p, gt.data(), gt.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        NM_CUDA(cudaStreamSynchronize(s));
+        auto t0 = std::chrono::steady_clock::now();
+        GammaTable table{L->gtab.as<double>(), gt.data(), Sa, b};
+        NM_TRY(filter_block(P, o->filter_prec, d, L->c, L->e, L->k_M, L->k_P, L->Ycat.as<double>(), B,
+                            L->Wcat.as<double>(), B, &table, L->fin, L->fout, s));
+        NM_CUDA(cudaStreamSynchronize(s));
+        L->t_filter += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (P->Mr.tma_state == 1) NM_TRY(tma_status(P->Mr.tma.err, s));
+        for (int g = 0; g < Sa; ++g) {
+            SliceState& z = L->st[act[g0 + g]];
+            const int j = z.j;
+            const int m = (j + 1) * b;
+            double* W = L->Wcat.as<double>() + g * b;   // ld B
+            // CGS2 against the slice's basis in the M inner product
+            NM_CUDA(cudaMemsetAsync(z.H.p, 0, (size_t)m * b * sizeof(double), s));
+            for (int pass = 0; pass < 2; ++pass) {
+                NM_TRY(apply_M_pub<double>(P, W, B, z.MW.as<double>(), b, b, KRON_PLAIN, nullptr, s));
+                NM_TRY(gemm_VtW(ctx, n, m, b, z.V.as<double>(), ldv, z.MW.as<double>(), b, z.C.as<double>(), 0.0));
+                NM_TRY(gemm_WmVC(ctx, n, m, b, -1.0, z.V.as<double>(), ldv, z.C.as<double>(), m, W, B));
+                const double one = 1.0;
+                NM_CUBLAS(cublasDaxpy(ctx->cublas, m * b, &one, z.C.as<double>(), 1, z.H.as<double>(), 1));
+            }
+            std::vector<double> hH((size_t)m * b);
+            NM_CUDA(cudaMemcpyAsync(hH.data(), z.H.p, hH.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+            double* Vn = z.V.as<double>() + (int64_t)(j + 1) * b;
+            NM_TRY(launch_scale_copy<double>(n, b, 1.0, W, B, Vn, ldv, s));
+            int ok = 1;
+            NM_TRY(m_orth(P, Vn, ldv, b, z.MW.as<double>(), z.G.as<double>(), &ok, s));
+            z.ok = ok != 0;
+            std::vector<double> hR((size_t)b * b);
+            NM_CUDA(cudaMemcpy(hR.data(), z.G.p, hR.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            for (int cc = 0; cc < b; ++cc)
+                for (int r = 0; r < m; ++r)
+                    z.Tfull[(size_t)r + (size_t)(j * b + cc) * mmax] = hH[(size_t)r + (size_t)cc * m];
+            z.j = j + 1;
+            z.blocks = j + 1;
+            z.m_used = m;
+            std::vector<double> Tm((size_t)m * m);
             for (int r = 0; r < m; ++r)
-                z.Tfull[(size_t)r + (size_t)(j * b + cc) * mmax] = hH[(size_t)r + (size_t)cc * m];
-        z.blocks = j + 1;
-        z.m_used = m;
-        std::vector<double> Tm((size_t)m * m);
-        for (int r = 0; r < m; ++r)
-            for (int cc = 0; cc < m; ++cc)
-                Tm[(size_t)r + (size_t)cc * m] = r <= cc ? z.Tfull[(size_t)r + (size_t)cc * mmax]
-                                                         : z.Tfull[(size_t)cc + (size_t)r * mmax];
-        DevBuf Td, wd;
-        NM_TRY(Td.alloc(Tm.size() * sizeof(double)));
-        NM_TRY(wd.alloc(m * sizeof(double)));
-        NM_CUDA(cudaMemcpy(Td.p, Tm.data(), Tm.size() * sizeof(double), cudaMemcpyHostToDevice));
-        NM_TRY(dense_eig(ctx, m, Td.as<double>(), nullptr, wd.as<double>()));
-        std::vector<double> th(m), Sv((size_t)m * m);
-        NM_CUDA(cudaMemcpy(th.data(), wd.p, m * sizeof(double), cudaMemcpyDeviceToHost));
-        NM_CUDA(cudaMemcpy(Sv.data(), Td.p, Sv.size() * sizeof(double), cudaMemcpyDeviceToHost));
-        int nwanted = 0, nconv = 0;
-        for (int i = 0; i < m; ++i) {
-            if (th[i] < z.tau) continue;
-            ++nwanted;
-            double r2 = 0;
-            if (ok)
-                for (int r = 0; r < b; ++r) {
-                    double v = 0;
-                    for (int qq = r; qq < b; ++qq)
-                        v += hR[(size_t)r + (size_t)qq * b] * Sv[(size_t)(m - b + qq) + (size_t)i * m];
-                    r2 += v * v;
-                }
-            if (std::sqrt(r2) <= L->conv_T * std::max(std::fabs(th[i]), 1.0)) ++nconv;
-        }
-        z.nwanted = nwanted;
-        z.nconv = nconv;
-        if (o->log_every > 0 && (j + 1) % o->log_every == 0)
-            fprintf(stderr, "[nm] slice %d block %d m=%d wanted=%d converged=%d filter %.1fs total %.1fs\n", act[g],
-                    j + 1, m, nwanted, nconv, L->t_filter,
-                    std::chrono::duration<double>(std::chrono::steady_clock::now() - L->t_start).count());
-        const bool last = j + 1 == o->max_blocks || !ok;
-        if ((nwanted > 0 && nconv == nwanted && (j + 1) % L->check == 0) || last) {
-            if (!z.R) {
-                z.R = new (std::nothrow) nm_result();
-                if (!z.R) return fail(NM_ENOMEM, "host allocation failed");
+                for (int cc = 0; cc < m; ++cc)
+                    Tm[(size_t)r + (size_t)cc * m] = r <= cc ? z.Tfull[(size_t)r + (size_t)cc * mmax]
+                                                             : z.Tfull[(size_t)cc + (size_t)r * mmax];
+            DevBuf Td, wd;
+            NM_TRY(Td.alloc(Tm.size() * sizeof(double)));
+            NM_TRY(wd.alloc(m * sizeof(double)));
+            NM_CUDA(cudaMemcpy(Td.p, Tm.data(), Tm.size() * sizeof(double), cudaMemcpyHostToDevice));
+            NM_TRY(dense_eig(ctx, m, Td.as<double>(), nullptr, wd.as<double>()));
+            std::vector<double> th(m), Sv((size_t)m * m);
+            NM_CUDA(cudaMemcpy(th.data(), wd.p, m * sizeof(double), cudaMemcpyDeviceToHost));
+            NM_CUDA(cudaMemcpy(Sv.data(), Td.p, Sv.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            int nwanted = 0, nconv = 0;
+            for (int i = 0; i < m; ++i) {
+                if (th[i] < z.tau) continue;
+                ++nwanted;
+                double r2 = 0;
+                if (ok)
+                    for (int r = 0; r < b; ++r) {
+                        double v = 0;
+                        for (int qq = r; qq < b; ++qq)
+                            v += hR[(size_t)r + (size_t)qq * b] * Sv[(size_t)(m - b + qq) + (size_t)i * m];
+                        r2 += v * v;
+                    }
+                if (std::sqrt(r2) <= L->conv_T * std::max(std::fabs(th[i]), 1.0)) ++nconv;
             }
-            NM_TRY(rayleigh_ritz(P, z.V.as<double>(), ldv, m, z.lam_lo, z.lam_hi, &z.R->X, z.rr));
-            bool all = z.rr.k > 0;
-            for (double r : z.rr.res) all = all && r <= L->tol;
-            if (all || last) {
-                z.converged = all;
-                z.active = false;
+            z.nwanted = nwanted;
+            z.nconv = nconv;
+            if (o->log_every > 0 && (j + 1) % o->log_every == 0)
+                fprintf(stderr, "[nm] slice %d block %d m=%d wanted=%d converged=%d filter %.1fs total %.1fs\n",
+                        act[g0 + g],
+                        j + 1, m, nwanted, nconv, L->t_filter,
+                        std::chrono::duration<double>(std::chrono::steady_clock::now() - L->t_start).count());
+            const bool last = j + 1 == o->max_blocks || !ok;
+            if ((nwanted > 0 && nconv == nwanted && (j + 1) % L->check == 0) || last) {
+                if (!z.R) {
+                    z.R = new (std::nothrow) nm_result();
+                    if (!z.R) return fail(NM_ENOMEM, "host allocation failed");
+                }
+                NM_TRY(rayleigh_ritz(P, z.V.as<double>(), ldv, m, z.lam_lo, z.lam_hi, &z.R->X, z.rr));
+                bool all = z.rr.k > 0;
+                for (double r : z.rr.res) all = all && r <= L->tol;
+                if (all || last) {
+                    z.converged = all;
+                    z.active = false;
+                }
             }
         }
     }
-    L->j = j + 1;
+    L->j += 1;
     *active_out = lanczos_active(L);
     return NM_OK;
 }
 
-// Results of every slice (a Rayleigh-Ritz on the current basis of the
-// slices that have none yet). NM_ENOTCONV if a slice did not pass tol; the
-// results are returned all the same. Ownership of the results moves to the
-// caller; the run keeps no reference to them.
-int lanczos_finish(nm_lanczos* L, nm_result** out) {
+// Result of slice q (a Rayleigh-Ritz on its current basis if it has none
+// yet); the slice leaves the run and its basis is released.
+static int slice_result(nm_lanczos* L, SliceState& z, nm_result** out) {
     nm_problem* P = L->P;
-    const int64_t n = P->info.n;
-    for (int q = 0; q < L->S; ++q) out[q] = nullptr;
-    int rc = NM_OK;
-    for (int q = 0; q < L->S; ++q) {
-        SliceState& z = L->st[q];
-        if (!z.R) {
-            z.R = new (std::nothrow) nm_result();
-            if (!z.R) return fail(NM_ENOMEM, "host allocation failed");
-            if (z.m_used > 0) {
-                NM_TRY(rayleigh_ritz(P, z.V.as<double>(), L->ldv, z.m_used, z.lam_lo, z.lam_hi, &z.R->X, z.rr));
-            } else {
-                // no block step taken: the start block is the basis
-                NM_TRY(rayleigh_ritz(P, z.V.as<double>(), L->ldv, L->b, z.lam_lo, z.lam_hi, &z.R->X, z.rr));
-                z.m_used = L->b;
-            }
+    *out = nullptr;
+    if (!z.R) {
+        z.R = new (std::nothrow) nm_result();
+        if (!z.R) return fail(NM_ENOMEM, "host allocation failed");
+        if (z.m_used > 0) {
+            NM_TRY(rayleigh_ritz(P, z.V.as<double>(), L->ldv, z.m_used, z.lam_lo, z.lam_hi, &z.R->X, z.rr));
+        } else {
+            // no block step taken: the start block is the basis
+            NM_TRY(rayleigh_ritz(P, z.V.as<double>(), L->ldv, L->b, z.lam_lo, z.lam_hi, &z.R->X, z.rr));
+            z.m_used = L->b;
         }
-        nm_result* R = z.R;
-        R->lambda = z.rr.lam;
-        R->resid = z.rr.res;
-        R->info.k = z.rr.k;
-        R->info.n = n;
-        R->info.blocks = z.blocks;
-        R->info.m = z.m_used;
-        R->info.filter_applications = (int64_t)z.blocks * L->b;
-        R->info.lam_lo = L->blo;
-        R->info.lam_hi = L->bhi;
-        R->info.seconds_filter = L->t_filter;
-        R->info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - L->t_start).count();
-        if (!z.converged) rc = NM_ENOTCONV;
     }
-    for (int q = 0; q < L->S; ++q) {
-        out[q] = L->st[q].R;
-        L->st[q].R = nullptr;
+    nm_result* R = z.R;
+    R->lambda = z.rr.lam;
+    R->resid = z.rr.res;
+    R->info.k = z.rr.k;
+    R->info.n = P->info.n;
+    R->info.blocks = z.blocks;
+    R->info.m = z.m_used;
+    R->info.filter_applications = (int64_t)z.blocks * L->b;
+    R->info.lam_lo = L->blo;
+    R->info.lam_hi = L->bhi;
+    R->info.seconds_filter = L->t_filter;
+    R->info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - L->t_start).count();
+    z.R = nullptr;
+    z.active = false;
+    z.taken = true;
+    for (DevBuf* buf : {&z.V, &z.MW, &z.C, &z.H, &z.G}) buf->release();
+    std::vector<double>().swap(z.Tfull);
+    *out = R;
+    return NM_OK;
+}
+
+// Results of every slice not taken yet (out[q] = nullptr for taken ones).
+// NM_ENOTCONV if a slice did not pass tol; the results are returned all the
+// same. Ownership of the results moves to the caller.
+int lanczos_finish(nm_lanczos* L, nm_result** out) {
+    const int S = (int)L->st.size();
+    for (int q = 0; q < S; ++q) out[q] = nullptr;
+    int rc = NM_OK;
+    for (int q = 0; q < S; ++q) {
+        SliceState& z = L->st[q];
+        if (z.taken) continue;
+        const bool conv = z.converged;
+        NM_TRY(slice_result(L, z, out + q));
+        if (!conv) rc = NM_ENOTCONV;
     }
     if (rc != NM_OK) return fail(rc, "a slice did not converge within max_blocks");
     return NM_OK;
 }
 
+int lanczos_take(nm_lanczos* L, int q, nm_result** out) {
+    *out = nullptr;
+    if (q < 0 || q >= (int)L->st.size()) return fail(NM_EINVAL, "slice index out of range");
+    SliceState& z = L->st[q];
+    if (z.taken) return fail(NM_EINVAL, "slice already taken");
+    const bool conv = z.converged;
+    NM_TRY(slice_result(L, z, out));
+    if (!conv) return fail(NM_ENOTCONV, "the slice did not converge (its current Ritz pairs are returned)");
+    return NM_OK;
+}
+
+int lanczos_add(nm_lanczos* L, double lam_lo, double lam_hi, uint64_t seed, const double* start, int* index) {
+    *index = -1;
+    if (!(lam_hi > lam_lo)) return fail(NM_EINVAL, "slice needs lo < hi");
+    L->st.emplace_back();
+    const int q = (int)L->st.size() - 1;
+    const int rc = slice_init(L, L->st[q], lam_lo, lam_hi, start, seed);
+    if (rc != NM_OK) {
+        SliceState& z = L->st[q];
+        z.active = false;
+        z.taken = true;
+        for (DevBuf* buf : {&z.V, &z.MW, &z.C, &z.H, &z.G}) buf->release();
+        return rc;
+    }
+    NM_CUDA(cudaStreamSynchronize(L->P->ctx->stream));
+    *index = q;
+    return NM_OK;
+}
+
+int lanczos_nslices(const nm_lanczos* L) { return (int)L->st.size(); }
+
 int lanczos_state(const nm_lanczos* L, int slice, nm_lanczos_info* out) {
-    if (slice < 0 || slice >= L->S) return fail(NM_EINVAL, "slice index out of range");
+    if (slice < 0 || slice >= (int)L->st.size()) return fail(NM_EINVAL, "slice index out of range");
     const SliceState& z = L->st[slice];
     out->blocks = z.blocks;
     out->m = z.m_used;
-    out->active = z.active && L->j < L->o.max_blocks ? 1 : 0;
+    out->active = slice_running(L, z) ? 1 : 0;
     out->converged = z.converged ? 1 : 0;
     out->wanted = z.nwanted;
     out->ritz_converged = z.nconv;

@@ -32,6 +32,7 @@ EXPORTS = (
     "nm_profile", "nm_profile_read", "nm_kernel_launches", "nm_set_option", "nm_autotune",
     "nm_lanczos_multi", "nm_filter_apply_static", "nm_lanczos_begin", "nm_lanczos_step",
     "nm_lanczos_get_info", "nm_lanczos_finish", "nm_lanczos_free", "nm_gemm_tn", "nm_gemm_nn",
+    "nm_lanczos_add", "nm_lanczos_take",
 )
 
 
@@ -122,6 +123,8 @@ def _load():
         "nm_lanczos_get_info": [vp, i32, C.POINTER(nm_lanczos_info)],
         "nm_lanczos_finish": [vp, vp],
         "nm_lanczos_free": [vp],
+        "nm_lanczos_add": [vp, dbl, dbl, i32, C.c_uint64, vp, C.POINTER(i32)],
+        "nm_lanczos_take": [vp, i32, C.POINTER(vp)],
         "nm_gemm_tn": [vp, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp],
         "nm_gemm_nn": [vp, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, vp],
     }
@@ -485,7 +488,8 @@ class Problem:
 
 
 class LanczosRun:
-    """A resumable block Lanczos run (nm_lanczos_begin / step / finish)."""
+    """A resumable block Lanczos run (nm_lanczos_begin / step / add / take /
+    finish). Slices are numbered in the order they were begun or added."""
 
     def __init__(self, prob, h, nslices):
         self.prob = prob
@@ -504,13 +508,32 @@ class LanczosRun:
         _check(_lib.nm_lanczos_get_info(self.h, slice, C.byref(st)), self.prob.ctx.h)
         return {k: getattr(st, k) for k, _ in nm_lanczos_info._fields_}
 
+    def add(self, lo, hi, unit=NM_UNIT_OMEGA, seed=1, start=None):
+        """A slice joins the running batch; returns its slice number."""
+        idx = C.c_int()
+        _check(_lib.nm_lanczos_add(self.h, lo, hi, unit, seed, C.c_void_p(start.data_ptr()) if start is not None
+                                   else None, C.byref(idx)), self.prob.ctx.h)
+        self.nslices = max(self.nslices, idx.value + 1)
+        return idx.value
+
+    def take(self, slice, allow_unconverged=False):
+        """The Result of one slice, which leaves the run."""
+        h = C.c_void_p()
+        rc = _lib.nm_lanczos_take(self.h, slice, C.byref(h))
+        if rc != NM_OK and not (rc == NM_ENOTCONV and allow_unconverged and h.value):
+            if h.value:
+                _lib.nm_result_free(h)
+            _check(rc, self.prob.ctx.h)
+        return Result(self.prob.ctx, h)
+
     def finish(self, allow_unconverged=False):
-        """Results of every slice (list of Result); frees the run."""
+        """Results of every slice not taken yet (list of Result, in slice
+        order); frees the run."""
         hs = (C.c_void_p * self.nslices)()
         rc = _lib.nm_lanczos_finish(self.h, C.cast(hs, C.c_void_p))
         res = [Result(self.prob.ctx, C.c_void_p(h)) for h in hs if h]
         self.free()
-        if rc != NM_OK and not (rc == NM_ENOTCONV and allow_unconverged and len(res) == self.nslices):
+        if rc != NM_OK and not (rc == NM_ENOTCONV and allow_unconverged):
             for r in res:
                 r.free()
             _check(rc, self.prob.ctx.h)

@@ -1,23 +1,35 @@
 """Continuous-batching server for spectrum-slice requests on one GPU.
 
-Requests (a mesh + model, a slice, solver options) arrive at any time. A
-scheduler admits them FIFO as soon as a worker slot is idle and the
-request's estimated device memory fits the free HBM; admitted requests run
-concurrently, each slot on its own libnm context (own CUDA stream, cuBLAS
-and cuSOLVER handles), so their kernels overlap on the device while later
-arrivals wait. Assembled problems stay resident in the slot that built them
-and are reused by later requests for the same mesh; the least recently used
-ones are freed when memory is short. Every request records its arrival,
-admission and completion times, from which the latency percentiles follow.
+Requests (a mesh + model, a slice, solver options) arrive at any time. Each
+mesh is served by an engine: a worker thread with its own libnm context
+(CUDA stream, cuBLAS and cuSOLVER handles) holding the assembled problem
+resident, and at most one running filtered-Lanczos batch (nm_lanczos_begin /
+step / add / take). A request for a mesh joins its engine's running batch
+at the next block step when the options agree (block width, filter degree,
+inner steps, precision, limits) and the batch has room (64 columns); it
+leaves the batch as soon as its slice converges, while the others keep
+stepping. Requests that cannot join wait for the engine's next batch.
+Engines of different meshes run concurrently, so their kernels overlap on
+the device.
 
-The solves themselves are the library's (nm_lanczos_slice); this module only
-schedules them.
+Admission is by device memory: the scheduler keeps a ledger of committed
+bytes (resident problems with their filter scratch, and the Krylov bases
+of admitted slices), reserved when a request is admitted and released when
+its slice is taken or its problem evicted, and admits a request only when
+it fits both the ledger (against the free memory at start, less a reserve)
+and the device's current free memory. Problem sizes come from the
+library's own counts (nm_problem_get_info) once a mesh has been assembled,
+and from the mesh's tet count before. Idle engines are evicted least
+recently used when memory is short. Every request records its arrival,
+admission and completion times, from which the latency percentiles
+follow.
+
+The solves themselves are the library's; this module only schedules them.
 """
 from __future__ import annotations
 
 import collections
 import dataclasses
-import queue
 import threading
 import time
 from typing import Any, Callable, Optional
@@ -26,13 +38,17 @@ import numpy as np
 
 from . import nm
 
+# options that must agree for requests to share one batch
+_BATCH_KEYS = ("block", "degree", "k_M", "k_P", "max_blocks", "check_every", "prec", "tol", "bounds_steps")
+_MAX_COLS = 64
+
 
 @dataclasses.dataclass
 class Request:
     key: str                       # mesh identity (problems are cached by it)
     build: Callable[[], Any]       # returns (mesh, model) when the problem must be assembled
     interval: tuple                # (omega_lo, omega_hi)
-    opts: dict                     # keyword arguments of Problem.lanczos_slice
+    opts: dict                     # block, degree, k_M, k_P, max_blocks, check_every, prec, tol, seed
     t_arrival: float = 0.0
     t_admit: float = 0.0
     t_done: float = 0.0
@@ -41,8 +57,10 @@ class Request:
     info: Optional[dict] = None
     error: Optional[str] = None
     done: threading.Event = dataclasses.field(default_factory=threading.Event)
-    slot: int = -1
+    slot: int = -1                 # engine index that served it
     run_bytes: int = 0
+    joined: bool = False           # joined a batch that was already running
+    n_dof_hint: int = 0
 
     @property
     def latency(self):
@@ -55,98 +73,238 @@ def _device_free_bytes(device):
     return free
 
 
-class _Slot(threading.Thread):
-    def __init__(self, server, index):
-        super().__init__(daemon=True, name=f"nm-slot-{index}")
+def _batch_sig(opts):
+    return tuple(opts.get(k) for k in _BATCH_KEYS)
+
+
+def problem_bytes(info):
+    """Device bytes of a resident problem from the library's counts: the
+    FP64 matrices, their float and double-float copies, the reference field
+    and the filter recurrence scratch of a full 64-column batch."""
+    nnz_u, nnz_p, nnz_e = info["nnz_u"], info["nnz_p"], info["nnz_e"]
+    n, Np, Nu = info["n"], info["Np"], info["Nu"]
+    mats = nnz_u * (9 * 8 + 4 + 8 + 2 * 9 * 4 + 3 * 4) + nnz_p * (8 + 4 + 3 * 4) + 2 * nnz_e * (3 * 8 + 4)
+    mats += 4 * (Nu + Np) * 8 + 3 * Nu * 8
+    scratch = (n * _MAX_COLS) * (3 * 8 + 7 * 4) + Np * _MAX_COLS * 3 * 8
+    return int(1.2 * (mats + scratch))
+
+
+def slice_bytes(n, opts):
+    """Device bytes of one slice in a batch: its Krylov basis, the block
+    buffers, and the Rayleigh-Ritz products (K V, M V and the Ritz vectors)."""
+    b = opts.get("block", 16)
+    m = b * (opts.get("max_blocks", 40) + 1)
+    return int(n * 8 * (m + 4 * b + 2 * m + m // 2))
+
+
+class _Engine(threading.Thread):
+    """One mesh: resident problem, at most one running batch."""
+
+    def __init__(self, server, index, key):
+        super().__init__(daemon=True, name=f"nm-engine-{index}")
         self.server = server
         self.index = index
-        self.inbox = queue.Queue()
-        self.problems = collections.OrderedDict()   # key -> Problem (LRU)
-        self.prob_bytes = {}                         # key -> bytes reserved for the resident problem
+        self.key = key
+        self.queue = collections.deque()      # admitted requests not yet in a batch
+        self.members = {}                     # slice number -> request of the running batch
+        self.batch = None
+        self.sig = None
+        self.prob = None
         self.ctx = None
-        self.busy = False
+        self.info = None
+        self.prob_bytes = 0                   # ledger entry of the resident problem
+        self.last_used = time.perf_counter()
+        self.max_batch = 0
+        self._wake = threading.Event()
+        self._halt = False
 
-    def run(self):
+    # -- scheduler side (called under server._lock)
+    def busy(self):
+        return self.batch is not None or bool(self.queue) or bool(self.members)
+
+    def post(self, req):
+        self.queue.append(req)
+        self.last_used = time.perf_counter()
+        self._wake.set()
+
+    def stop(self):
+        self._halt = True
+        self._wake.set()
+
+    # -- engine thread
+    def run(self):  # noqa: C901  (one loop: assemble, batch, step, take)
         import torch
         torch.cuda.set_device(self.server.device)
         self.ctx = nm.Context(self.server.device)
         while True:
-            req = self.inbox.get()
-            if req is None:
-                break
-            try:
-                P = self.problems.get(req.key)
-                if P is None:
-                    mesh, model = req.build()
-                    P = nm.Problem(self.ctx, mesh, model)
-                    self.problems[req.key] = P
-                self.problems.move_to_end(req.key)
-                P.set_interval(*req.interval)
-                res = P.lanczos_slice(allow_unconverged=True, **req.opts)
-                req.lam, req.resid, req.info = res.lam.copy(), res.resid.copy(), dict(res.info)
-                res.free()
-            except Exception as ex:  # reported on the request, the slot keeps serving
-                req.error = repr(ex)
-            req.t_done = time.perf_counter()
             with self.server._lock:
-                self.server._running_bytes -= req.run_bytes
-            self.busy = False
-            req.done.set()
-            self.server._wake.set()
-        for P in self.problems.values():
-            P.free()
+                pending = list(self.queue)
+                if self._halt and not pending and not self.members:
+                    break
+            if not pending and not self.members:
+                self._wake.wait(0.05)
+                self._wake.clear()
+                continue
+            try:
+                self._ensure_problem(pending)
+            except Exception as ex:  # the requests of this mesh fail, the server keeps serving
+                self._fail_all(repr(ex))
+                continue
+            self._admit_pending()
+            if not self.members:
+                continue
+            try:
+                self.batch.step()
+                self._take_finished()
+            except Exception as ex:
+                self._fail_members(repr(ex))
+        self._release_problem()
         self.ctx.close()
 
-    def evict_one(self):
-        """Free the least recently used resident problem of an idle slot."""
-        if self.problems and not self.busy:
-            key, P = self.problems.popitem(last=False)
-            self.prob_bytes.pop(key, None)
-            P.free()
-            return True
-        return False
+    def _ensure_problem(self, pending):
+        if self.prob is not None or not pending:
+            return
+        mesh, model = pending[0].build()
+        self.prob = nm.Problem(self.ctx, mesh, model)
+        self.info = dict(getattr(self.prob, "info", {}) or {})
+        if self.info:
+            with self.server._lock:
+                exact = problem_bytes(self.info)
+                self.server._known_sizes[self.key] = self.info
+                self.prob_bytes = exact
+
+    def _admit_pending(self):
+        """Start a batch with the first queued request or let queued
+        requests join the running one."""
+        with self.server._lock:
+            batch = []
+            while self.queue:
+                req = self.queue[0]
+                b = req.opts.get("block", 16)
+                if self.batch is None and not batch:
+                    batch.append(self.queue.popleft())
+                    continue
+                sig = self.sig if self.batch is not None else _batch_sig(batch[0].opts)
+                if _batch_sig(req.opts) != sig or (len(self.members) + len(batch) + 1) * b > _MAX_COLS:
+                    break
+                batch.append(self.queue.popleft())
+        if not batch:
+            return
+        for req in batch:
+            lo, hi = req.interval
+            try:
+                if self.batch is None:
+                    o = {k: v for k, v in req.opts.items() if k not in ("seed",)}
+                    self.batch = self.prob.lanczos_begin([(lo, hi)], seed=req.opts.get("seed", 1), **o)
+                    self.sig = _batch_sig(req.opts)
+                    q = 0
+                else:
+                    q = self.batch.add(lo, hi, seed=req.opts.get("seed", 1))
+                    req.joined = True
+                self.members[q] = req
+                self.max_batch = max(self.max_batch, len(self.members))
+            except Exception as ex:
+                self._complete(req, error=repr(ex))
+
+    def _take_finished(self):
+        for q, req in list(self.members.items()):
+            if self.batch.info(q)["active"]:
+                continue
+            del self.members[q]
+            try:
+                res = self.batch.take(q, allow_unconverged=True)
+                self._complete(req, res=res)
+            except Exception as ex:
+                self._complete(req, error=repr(ex))
+        if not self.members and self.batch is not None:
+            self.batch.free()
+            self.batch = None
+            self.sig = None
+
+    def _complete(self, req, res=None, error=None):
+        if res is not None:
+            req.lam, req.resid, req.info = res.lam.copy(), res.resid.copy(), dict(res.info)
+            res.free()
+        req.error = error
+        req.t_done = time.perf_counter()
+        with self.server._lock:
+            self.server._slice_bytes -= req.run_bytes
+            req.run_bytes = 0
+        self.last_used = time.perf_counter()
+        req.done.set()
+        self.server._wake.set()
+
+    def _fail_members(self, msg):
+        for q, req in list(self.members.items()):
+            del self.members[q]
+            self._complete(req, error=msg)
+        if self.batch is not None:
+            try:
+                self.batch.free()
+            finally:
+                self.batch = None
+                self.sig = None
+
+    def _fail_all(self, msg):
+        with self.server._lock:
+            pending = list(self.queue)
+            self.queue.clear()
+        for req in pending:
+            self._complete(req, error=msg)
+        self._fail_members(msg)
+        self._release_problem()
+
+    def _release_problem(self):
+        if self.batch is not None:
+            self.batch.free()
+            self.batch = None
+        if self.prob is not None:
+            self.prob.free()
+            self.prob = None
+        with self.server._lock:
+            self.prob_bytes = 0
 
 
 class SliceServer:
-    """FIFO admission by free slot and free HBM; concurrent execution.
+    """Continuous batching over per-mesh engines, admission by device memory.
 
-    Admission keeps a ledger of committed bytes (the estimates of running
-    solves and of resident problems), reserved when a request is admitted
-    and released when it completes or its problem is evicted: a slot
-    allocates only after admission, so the device's free memory alone would
-    let several requests in on the same bytes. A request is admitted when
-    it fits both the ledger (against the free memory at start, less the
-    reserve) and the device's current free memory."""
+    slots: how many engines (meshes) may hold a resident problem at once;
+    requests for a mesh without an engine wait for a free engine (idle
+    engines are evicted least recently used)."""
 
     def __init__(self, slots=2, device=0, reserve_bytes=2 << 30):
         self.device = device
         self.reserve = reserve_bytes
+        self.max_engines = slots
         self._budget = _device_free_bytes(device) - reserve_bytes
-        self._running_bytes = 0
+        self._slice_bytes = 0
+        self._known_sizes = {}
         self.pending = collections.deque()
         self.all = []
-        self._lock = threading.Lock()
+        self.engines = {}          # key -> _Engine
+        self._retired = []
+        self._next_index = 0
+        self._lock = threading.RLock()
         self._wake = threading.Event()
         self._stop = False
-        self.slots = [_Slot(self, i) for i in range(slots)]
-        for s in self.slots:
-            s.start()
         self._sched = threading.Thread(target=self._loop, daemon=True, name="nm-scheduler")
         self._sched.start()
 
-    @staticmethod
-    def estimate_bytes(n_dof, opts, resident=False):
-        """Device memory a request needs beyond a resident problem (basis,
-        Rayleigh-Ritz products, filter scratch), plus the problem itself
-        when it is not resident yet (about 80 B per dof for the matrices)."""
-        b = opts.get("block", 16)
-        m = b * (opts.get("max_blocks", 40) + 1)
-        need = n_dof * 8 * (m + 2 * m + 8 * b)
-        if not resident:
-            need += 80 * n_dof * 30
-        return need
+    # -- memory estimates (overridable)
+    def estimate_bytes(self, req, resident):
+        """(problem bytes, slice bytes) of a request: the problem's share is
+        0 when its mesh is resident already."""
+        info = self._known_sizes.get(req.key)
+        if info is None:
+            tets = max(int(req.n_dof_hint), 1)
+            info = {"nnz_u": 40 * tets, "nnz_p": 12 * tets, "nnz_e": 10 * tets, "n": 5 * tets, "Np": tets,
+                    "Nu": 2 * tets}
+        prob = 0 if resident else problem_bytes(info)
+        return prob, slice_bytes(info["n"], req.opts)
 
     def submit(self, req: Request, n_dof_hint: int):
+        """Queue a request; n_dof_hint is the mesh's tet count (used until
+        the mesh has been assembled once)."""
         req.t_arrival = time.perf_counter()
         req.n_dof_hint = n_dof_hint
         with self._lock:
@@ -155,6 +313,27 @@ class SliceServer:
         self._wake.set()
         return req
 
+    def _committed(self):
+        return self._slice_bytes + sum(e.prob_bytes for e in self.engines.values())
+
+    def _fits(self, need):
+        return (self._committed() + need <= self._budget and
+                need <= _device_free_bytes(self.device) - self.reserve)
+
+    def _evict_idle(self, keep):
+        """Retire the least recently used idle engine (not `keep`)."""
+        idle = [e for k, e in self.engines.items() if k != keep and not e.busy()]
+        if not idle:
+            return False
+        e = min(idle, key=lambda x: x.last_used)
+        del self.engines[e.key]
+        e.stop()
+        self._retired.append(e)
+        # the ledger drops its problem now; the device's free memory, also
+        # checked at admission, follows once the engine has freed it
+        e.prob_bytes = 0
+        return True
+
     def _loop(self):
         while not self._stop:
             self._wake.wait(0.05)
@@ -162,36 +341,29 @@ class SliceServer:
             with self._lock:
                 while self.pending:
                     req = self.pending[0]
-                    idle = [s for s in self.slots if not s.busy]
-                    if not idle:
-                        break
-                    # prefer an idle slot that already holds the problem
-                    slot = next((s for s in idle if req.key in s.problems), idle[0])
-                    resident = req.key in slot.problems
-                    run = self.estimate_bytes(req.n_dof_hint, req.opts, True)
-                    prob = 0 if resident else self.estimate_bytes(req.n_dof_hint, req.opts, False) - run
-                    need = run + prob
-                    while not self._fits(need) and any(s.evict_one() for s in self.slots if s is not slot or
-                                                      not resident):
+                    eng = self.engines.get(req.key)
+                    resident = eng is not None
+                    prob, run = self.estimate_bytes(req, resident)
+                    if eng is None and len(self.engines) >= self.max_engines:
+                        if not self._evict_idle(keep=req.key):
+                            break          # every engine busy: wait (FIFO)
+                    while not self._fits(prob + run) and self._evict_idle(keep=req.key):
                         pass
-                    if not self._fits(need) and any(s.busy for s in self.slots):
-                        break        # wait for memory to be released by a running request
+                    if not self._fits(prob + run) and (self._slice_bytes > 0 or
+                                                        any(e.busy() for e in self.engines.values())):
+                        break              # wait for memory to be released by running slices
                     self.pending.popleft()
-                    self._running_bytes += run
+                    if eng is None:
+                        eng = _Engine(self, self._next_index, req.key)
+                        self._next_index += 1
+                        eng.prob_bytes = prob
+                        self.engines[req.key] = eng
+                        eng.start()
+                    self._slice_bytes += run
                     req.run_bytes = run
-                    if prob:
-                        slot.prob_bytes[req.key] = prob
                     req.t_admit = time.perf_counter()
-                    req.slot = slot.index
-                    slot.busy = True
-                    slot.inbox.put(req)
-
-    def _committed(self):
-        return self._running_bytes + sum(sum(s.prob_bytes.values()) for s in self.slots)
-
-    def _fits(self, need):
-        return (self._committed() + need <= self._budget and
-                need <= _device_free_bytes(self.device) - self.reserve)
+                    req.slot = eng.index
+                    eng.post(req)
 
     def drain(self, timeout=None):
         for r in list(self.all):
@@ -202,10 +374,13 @@ class SliceServer:
         self._stop = True
         self._wake.set()
         self._sched.join()
-        for s in self.slots:
-            s.inbox.put(None)
-        for s in self.slots:
-            s.join()
+        with self._lock:
+            engines = list(self.engines.values()) + self._retired
+            self.engines.clear()
+        for e in engines:
+            e.stop()
+        for e in engines:
+            e.join()
 
     def stats(self):
         done = [r for r in self.all if r.done.is_set() and r.error is None]
@@ -213,11 +388,15 @@ class SliceServer:
         pairs = sum(int(np.sum(r.resid <= 1e-6)) for r in done if r.resid is not None)
         t0 = min(r.t_arrival for r in self.all) if self.all else 0.0
         t1 = max(r.t_done for r in done) if done else 0.0
+        engines = list(self.engines.values()) + self._retired
         return {"requests": len(self.all), "completed": len(done),
                 "errors": sum(1 for r in self.all if r.error is not None),
                 "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                 "eigenpairs": pairs, "eigenpairs_per_s": pairs / max(t1 - t0, 1e-9),
-                "overlap_max": self.max_overlap()}
+                "overlap_max": self.max_overlap(),
+                "joined_running_batch": sum(1 for r in self.all if r.joined),
+                "max_batch": max([e.max_batch for e in engines], default=0),
+                "engines": len(engines)}
 
     def max_overlap(self):
         """Largest number of requests that were running at the same time."""

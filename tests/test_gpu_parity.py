@@ -585,8 +585,22 @@ def test_lanczos_multi_matches_single_slices(nm, ball, prec):
 def test_lanczos_multi_rejects_too_wide(nm, ball):
     w, S, P = ball
     with pytest.raises(nm.NMError) as e:
-        P.lanczos_multi([(0.0, 1.0)] * 5, block=16)
+        P.lanczos_multi([(0.0, 1.0)], block=65)
     assert e.value.code == nm.NM_EINVAL
+
+
+def test_lanczos_multi_more_than_64_columns(nm, ball):
+    """Three slices of 32 columns (96 > 64) are filtered in groups of two
+    and one per block step; each slice reaches the dense oracle's pairs."""
+    w, S, P = ball
+    K, M = eig.pencil_dense(S)
+    lam = eig.all_eigs(K, M)[0]
+    slices = [(0.0, 2.58), (2.58, 2.7), (2.7, 3.0)]
+    res = P.lanczos_multi(slices, block=32, degree=100, k_M=40, k_P=40, max_blocks=8, seed=4)
+    assert len(res) == 3
+    for (lo, hi), r in zip(slices, res):
+        l = -1e-8 * lam[-1] if lo == 0 else lo * lo
+        _check_slice(r, lam[(lam >= l) & (lam <= hi * hi)], lam[-1])
 
 
 # ------------------------------------------------------------------ resumable block Lanczos
@@ -814,3 +828,97 @@ def test_dense_tc_option_agrees_with_dgemm(nm, ball):
     assert len(a.lam) == len(b.lam) == 16
     lam_max = np.abs(a.lam).max()
     assert np.allclose(a.lam, b.lam, rtol=1e-12, atol=1e-12 * lam_max)
+
+
+# ------------------------------------------------------------------ continuous batching
+def test_slice_joining_a_running_batch(nm, ball):
+    """A slice added to a batch after two block steps (its own block counter,
+    the run's shared bounds and filter) reaches the dense oracle's
+    eigenpairs, as does the slice that was running; each equals the same
+    slice solved alone to 1e-10; taking a slice releases it while the other
+    keeps stepping."""
+    w, S, P = ball
+    K, M = eig.pencil_dense(S)
+    lam = eig.all_eigs(K, M)[0]
+    kw = dict(block=8, degree=100, k_M=40, k_P=40, max_blocks=16, seed=5, check_every=1)
+    run = P.lanczos_begin([(0.0, 2.7)], **kw)
+    run.step()
+    run.step()
+    j = run.add(2.7, 3.0, seed=77)
+    assert j == 1 and run.info(1)["blocks"] == 0 and run.info(0)["blocks"] == 2
+    done = {}
+    while len(done) < 2:
+        active = run.step()
+        for q in (0, 1):
+            if q not in done and not run.info(q)["active"]:
+                done[q] = run.take(q)
+        if active == 0:
+            break
+    assert sorted(done) == [0, 1]
+    assert run.finish() == []          # every slice was taken
+    for q, (lo, hi) in ((0, (0.0, 2.7)), (1, (2.7, 3.0))):
+        l = -1e-8 * lam[-1] if lo == 0 else lo * lo
+        ref = lam[(lam >= l) & (lam <= hi * hi)]
+        _check_slice(done[q], ref, lam[-1])
+        P.set_interval(lo, hi)
+        alone = P.lanczos_slice(**dict(kw, seed=5 if q == 0 else 77))
+        big = np.abs(alone.lam) > 1e-10 * lam[-1]
+        assert np.allclose(done[q].lam[big], alone.lam[big], rtol=1e-10)
+
+
+def test_take_running_slice_returns_current_ritz_pairs(nm, ball):
+    w, S, P = ball
+    run = P.lanczos_begin([(0.0, 3.0)], block=8, degree=100, k_M=40, k_P=40, max_blocks=16, seed=5)
+    run.step()
+    with pytest.raises(nm.NMError) as e:
+        run.take(0)
+    assert e.value.code == nm.NM_ENOTCONV
+    with pytest.raises(nm.NMError) as e:
+        run.take(0)                     # already taken
+    assert e.value.code == nm.NM_EINVAL
+    run2 = P.lanczos_begin([(0.0, 3.0)], block=8, degree=100, k_M=40, k_P=40, max_blocks=16, seed=5)
+    run2.step()
+    r = run2.take(0, allow_unconverged=True)
+    assert r.info["blocks"] == 1
+    with pytest.raises(nm.NMError) as e:
+        run2.add(1.0, 0.5)              # lo > hi
+    assert e.value.code == nm.NM_EINVAL
+    run2.free()
+
+
+# ------------------------------------------------------------------ rotating layered planet (Sec. 7)
+def test_rotating_planet_batched_mixed_matches_oracle(nm, ctx):
+    """Rotating three-layer planet (fluid core, reference gravity,
+    Omega = 0.06781 about z): two adjacent slices of the seismic spectrum
+    solved in one batched mixed-precision run, their Ritz vectors projected
+    onto the rotating problem (eq. sublinear0); the reduced frequencies match
+    the oracle's reduction built from the dense eigenvectors of the same
+    slices to 1e-8, and the frequencies come in +- pairs."""
+    from synth.model import OMEGA_EARTH_NONDIM
+    mesh, model = layered_planet(h=0.25, seed=7, omega=OMEGA_EARTH_NONDIM)
+    S = fem.assemble(mesh, model)
+    K, M = eig.pencil_dense(S)
+    lam = eig.all_eigs(K, M)[0]
+    hi = np.sqrt(lam[lam > 0.5])
+    s1 = (0.5 * (hi[3] + hi[4]), 0.5 * (hi[13] + hi[14]))
+    s2 = (s1[1], 0.5 * (hi[25] + hi[26]))
+    P = nm.Problem(ctx, mesh, model)
+    res = P.lanczos_multi([s1, s2], block=8, degree=400, k_M=20, k_P=20, max_blocks=30, seed=2, check_every=2,
+                          prec=nm.NM_MIXED)
+    Xs = [r.vectors() for r in res]
+    lam_e = np.concatenate([r.lam for r in res])
+    assert (np.concatenate([r.resid for r in res]) <= 1e-6).all()
+    Xe = torch.cat(Xs, dim=1).contiguous()
+    P.set_interval(s1[0], s2[1])
+    rot = P.ritz(Xe, mode=nm.NM_RITZ_ROTATING, lam_e=lam_e)
+    # oracle: the same slices' dense eigenpairs, reduced with R
+    w_ref, X_ref = eig.slice_eigs(K, M, s1[0] ** 2, s2[1] ** 2)
+    assert np.allclose(np.sort(lam_e), w_ref, rtol=1e-8)
+    wr, _ = eig.rotating_reduced(w_ref, X_ref.T @ (S.R @ X_ref))
+    wr = np.sort(wr[(wr >= s1[0]) & (wr <= s2[1])])
+    assert len(rot.lam) == len(wr) > 0
+    assert np.allclose(np.sort(rot.lam), wr, rtol=1e-8)
+    full = np.sort(eig.rotating_reduced(w_ref, X_ref.T @ (S.R @ X_ref))[0])
+    assert np.allclose(full, -full[::-1], atol=1e-12 * np.abs(full).max())
+    assert (rot.resid >= 0).all() and np.isfinite(rot.resid).all()
+    P.free()
