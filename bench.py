@@ -98,8 +98,12 @@ def parse(argv=None):
     ap.add_argument("--max-blocks", type=int, default=24)
     ap.add_argument("--degree", type=int, default=DEGREE)
     ap.add_argument("--k-m", type=int, default=0)
-    ap.add_argument("--profile-case", action="store_true",
-                    help="one short mixed filter application on the full matrices (for ncu captures)")
+    ap.add_argument("--profile-case", nargs="?", const="filter", choices=("filter", "gemm"), default=None,
+                    help="a short case for ncu captures: 'filter' = two mixed filter applications of degree 10 "
+                         "on the full matrices; 'gemm' = the tensor-core dense products of a 576-column basis "
+                         "on 200,003 rows")
+    ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
+                    help="problem option (nm_set_option), repeatable")
     ap.add_argument("--chunk", type=int, default=None,
                     help="chunked row schedule of the semi-iteration SpMMs (threads per CTA; 0 = off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -458,6 +462,9 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_1906_11082_gb300 import nm
 
+    if args.profile_case == "gemm":
+        gemm_case(nm, local)
+        return
     w = workload(args.h)
     ctx = nm.Context(local)
     torch.cuda.synchronize()
@@ -466,6 +473,9 @@ def run_ours(args):
     t_asm = time.perf_counter() - t_asm
     if args.chunk is not None:
         P.set_option("chunk", args.chunk)
+    for kv in args.option:
+        key, val = kv.split("=", 1)
+        P.set_option(key, int(val))
     prec = {"f64": nm.NM_F64, "f32": nm.NM_F32, "mixed": nm.NM_MIXED}[args.prec]
     k_M = args.k_m or K_INNER[args.prec]
     opts = dict(block=BLOCK, degree=args.degree, k_M=k_M, k_P=k_M, max_blocks=args.max_blocks, check_every=2,
@@ -650,6 +660,24 @@ def run_ours(args):
         except Exception as ex:
             line["cpu_baseline"] = {"error": repr(ex)}
     print(json.dumps(line))
+
+
+def gemm_case(nm, device):
+    """The dense products of the Lanczos and Ritz steps on a 200,003-row,
+    576-column basis: V^T W (576 x 32), V C (200,003 x 32), four of each."""
+    import torch
+    ctx = nm.Context(device)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    n, m, b = 200003, 576, 32
+    V = torch.randn((n, m), dtype=torch.float64, device="cuda", generator=g)
+    W = torch.randn((n, b), dtype=torch.float64, device="cuda", generator=g)
+    C = torch.empty((b, m), dtype=torch.float64, device="cuda")
+    D = torch.empty((n, b), dtype=torch.float64, device="cuda")
+    for _ in range(4):
+        ctx.gemm_tn(V, W, C)
+        ctx.gemm_nn(V, C, D)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "gemm", "n": n, "m": m, "b": b}))
 
 
 def run_serving(args, device):
