@@ -238,8 +238,14 @@ def rel_residuals(KX, MX, lam, floor):
     return r / den
 
 
-def rayleigh_ritz(op: Operator, V, lam_lo, lam_hi):
-    """Ritz pairs of the pencil (K_eff, M) on span(V) inside [lam_lo, lam_hi]."""
+def rayleigh_ritz(op: Operator, V, lam_lo, lam_hi, Sw=None):
+    """Ritz pairs of the pencil (K_eff, M) on span(V) inside [lam_lo, lam_hi].
+
+    Sw (m x nw, orthonormal columns): coefficients of the converged Ritz
+    vectors of p(B) above the threshold. Then only the pairs whose
+    coefficient vector lies at least half in span(Sw) are kept; the others
+    are spurious Ritz values of the whole basis (mixtures of directions from
+    both sides of the slice)."""
     KV = op.K_exact(V)
     MV = op.M @ V
     H = V.T @ KV
@@ -248,6 +254,9 @@ def rayleigh_ritz(op: Operator, V, lam_lo, lam_hi):
     G = 0.5 * (G + G.T)
     w, S = sla.eigh(H, G)
     sel = (w >= lam_lo) & (w <= lam_hi)
+    if Sw is not None:
+        frac = np.sum((Sw.T @ S) ** 2, axis=0) / np.sum(S ** 2, axis=0)
+        sel &= frac >= 0.5
     X = V @ S[:, sel]
     lam = w[sel]
     res = rel_residuals(KV @ S[:, sel], MV @ S[:, sel], lam, residual_floor(lam_lo, lam_hi))
@@ -260,7 +269,10 @@ def lanczos_slice(op: Operator, lam_lo, lam_hi, d, b, max_blocks, seed=0,
 
     Returns (lam, X, resid, info). Stops when every Ritz value of p(B) above
     the filter threshold tau has converged and the pencil Rayleigh-Ritz on
-    the basis finds all of them with residual <= tol.
+    the basis finds the slice's pairs with residual <= tol, counting only
+    the pairs that lie in the span of those converged Ritz vectors (the
+    eigenpairs of the filtered Lanczos that Sec. 6.2 adopts come from the
+    Ritz vectors of the filtered operator above the threshold).
     """
     n = op.M.shape[0]
     if bounds is None:
@@ -301,7 +313,7 @@ def lanczos_slice(op: Operator, lam_lo, lam_hi, d, b, max_blocks, seed=0,
         conv = wanted & (resid_est <= 1e-8 * np.maximum(np.abs(th), 1.0))
         basis.append(Q)
         if (j + 1) % check_every == 0 and wanted.any() and conv.sum() == wanted.sum():
-            lam, X, res = rayleigh_ritz(op, Vall, lam_lo, lam_hi)
+            lam, X, res = rayleigh_ritz(op, Vall, lam_lo, lam_hi, Sw=S[:, wanted])
             if len(lam) and np.all(res <= tol):
                 info['m'] = m
                 return lam, X, res, info
