@@ -71,12 +71,16 @@ SERVING_SLICES = [(4.0, 5.5), (4.5, 6.0), (3.5, 5.0)]
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the
 # float mass-step kernel (kron_v4_kernel<3, 1, 32>) on this workload (same
-# matrices, b = 32), captured with `ncu --set full --clock-control none -k
-# regex:kron_v4_kernel -s 4 -c 2` around `bench.py --profile-case`, and the
-# SHA-256 of kernels.cu when it was taken: once the kernel source changes
-# the figure no longer describes it and the bench reports traffic null.
-TRAFFIC_CAPTURE = {"kernel": "kron_v4_kernel<3, 1, 32>", "bytes": 543_801_344 + 123_877_376,
-                   "kernels_cu_sha256": None}
+# matrices, b = 32; mean of two launches), captured with
+#   ncu --kernel-name-base demangled --metrics gpu__time_duration.sum,\
+#       dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
+#       -k 'regex:kron_v4_kernel<\(int\)3' -s 4 -c 2 --csv \
+#       python bench.py --profile-case filter
+# and the SHA-256 of kernels.cu when it was taken: once the kernel source
+# changes the figure no longer describes it and the bench reports traffic
+# null.
+TRAFFIC_CAPTURE = {"kernel": "kron_v4_kernel<3, 1, 32>", "bytes": 543_591_808 + 121_877_248,
+                   "kernels_cu_sha256": "2d86c3f12eacd75a3d36d4645078875c2e42d76cb1c6fc99cd683f8038ef0bf0"}
 
 # FP64 peak of GB300 (NVIDIA's published B300 figure, 1.25 TFLOP/s; equal to
 # 152 SMs x ~2.05 GHz x 2 FP64 FMA per SM per clock x 2 flop).
@@ -98,10 +102,13 @@ def parse(argv=None):
     ap.add_argument("--max-blocks", type=int, default=24)
     ap.add_argument("--degree", type=int, default=DEGREE)
     ap.add_argument("--k-m", type=int, default=0)
-    ap.add_argument("--profile-case", nargs="?", const="filter", choices=("filter", "gemm"), default=None,
+    ap.add_argument("--profile-case", nargs="?", const="filter", choices=("filter", "gemm", "selfgrav"),
+                    default=None,
                     help="a short case for ncu captures: 'filter' = two mixed filter applications of degree 10 "
                          "on the full matrices; 'gemm' = the tensor-core dense products of a 576-column basis "
-                         "on 200,003 rows")
+                         "on 200,003 rows; 'selfgrav' = K_eff products with and without the self-gravitation "
+                         "term on a planet of --sg-h (timed, one JSON line)")
+    ap.add_argument("--sg-h", type=float, default=0.15, help="mesh size of the 'selfgrav' profile case")
     ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
                     help="problem option (nm_set_option), repeatable")
     ap.add_argument("--chunk", type=int, default=None,
@@ -465,6 +472,9 @@ def run_ours(args):
     if args.profile_case == "gemm":
         gemm_case(nm, local)
         return
+    if args.profile_case == "selfgrav":
+        selfgrav_case(nm, local, args.sg_h)
+        return
     w = workload(args.h)
     ctx = nm.Context(local)
     torch.cuda.synchronize()
@@ -678,6 +688,44 @@ def gemm_case(nm, device):
         ctx.gemm_nn(V, C, D)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": "gemm", "n": n, "m": m, "b": b}))
+
+
+def selfgrav_case(nm, device, h, b=32, reps=5):
+    """K_eff X with and without -C^T S C (FP64, b columns) on the layered
+    planet of mesh size h, timed with CUDA events on the launching stream.
+    The N-body sum over the np charge points dominates the term; its
+    algorithmic FP64 work per product is np^2 (9 + 2 b) flops (distance
+    and 1/r once per pair, one FMA per pair and column)."""
+    import torch
+    from synth.model import layered_planet
+    mesh, model = layered_planet(h=h, seed=2)
+    ctx = nm.Context(device)
+    P0 = nm.Problem(ctx, mesh, model)
+    P1 = nm.Problem(ctx, mesh, model, self_gravity=True)
+    X = torch.randn((P0.n, b), dtype=torch.float64, device="cuda")
+    Y = torch.empty_like(X)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for key, P in (("cowling", P0), ("self_gravity", P1)):
+        for _ in range(2):
+            P.apply_K(X, Y, k_P=20)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(reps):
+            P.apply_K(X, Y, k_P=20)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        out[key] = ev[0].elapsed_time(ev[1]) / reps
+    n_pts = P1.info["n_charges"]
+    tet = np.asarray(mesh.tet)
+    sg_ms = out["self_gravity"] - out["cowling"]
+    flops = float(n_pts) ** 2 * (9 + 2 * b)
+    print(json.dumps({"profile_case": "selfgrav", "h": h, "tets": len(tet), "n": P0.n, "points": n_pts, "b": b,
+                      "k_eff_ms": out["cowling"], "full_ms": out["self_gravity"], "selfgrav_ms": sg_ms,
+                      "nbody_tflops": flops / (sg_ms * 1e-3) / 1e12 if sg_ms > 0 else None,
+                      "fp64_peak_tflops": FP64_PEAK_TFLOPS}))
+    ctx.close()
 
 
 def run_serving(args, device):

@@ -66,6 +66,19 @@ typedef enum { NM_RITZ_PENCIL = 0, NM_RITZ_ROTATING = 1 } nm_ritz_mode;
 /* flags of nm_model */
 #define NM_GRAVITY       1u   /* include the reference-gravity terms of A_G and E_G */
 #define NM_CENTRIFUGAL   2u   /* g' = g - grad psi: not supported (NM_EUNSUPPORTED) */
+/* Self-gravitation: the full operator K_eff - C^T S C of Sec. 5.2 (eqs.
+ * ph1body2, ph1surface2, phi1fluidsolid, eigfull) instead of the Cowling
+ * approximation. C maps u to the point masses of the elements
+ * (rho_k int_K div u at the barycentre) and of the outer-boundary and
+ * fluid-solid faces (the density jump times int_E nu . u, at the face
+ * barycentre); S is G / |r_i - r_j| between points and G / R_i on the
+ * diagonal, 1/R_i the mean of 1/|x - r_i| over the point's own element or
+ * face. Applied by a direct FP64 sum over the points (O(points^2) per
+ * column, points ~ tets + boundary faces; its point buffers, 2 * 64
+ * doubles per point, are allocated at assembly). Supported with NM_F64 and
+ * NM_MIXED (the term is applied in double); NM_F32 products return
+ * NM_EUNSUPPORTED. */
+#define NM_SELF_GRAVITY  4u
 
 typedef struct nm_ctx nm_ctx;
 typedef struct nm_problem nm_problem;
@@ -111,6 +124,7 @@ typedef struct {
     int64_t nnz_p;     /* stored entries of A_p                             */
     int64_t nnz_e;     /* stored 3x1 blocks of E_G                          */
     int64_t n_fs;      /* fluid-solid interface faces                       */
+    int64_t n_charges; /* charge points of NM_SELF_GRAVITY (0 without it)   */
 } nm_problem_info;
 
 /* Filter for nm_filter_apply: Z = sum_{k=0..degree} gamma[k] T_k(B) Y with
@@ -256,9 +270,12 @@ int nm_apply_R(nm_problem* prob, const void* X, int64_t ldx, void* Y, int64_t ld
 
 /* ---- slice set-up ------------------------------------------------------
  * Store the target interval (eq. freq): unit NM_UNIT_OMEGA takes angular
- * frequencies (lambda = omega^2; a negative lo means lambda_lo = -lo^2 is
- * NOT used: lo < 0 is clamped to -1e-8 * lambda_max at solve time),
- * NM_UNIT_OMEGA2 takes lambda directly. */
+ * frequencies (lambda = omega^2; lo <= 0 means lambda_lo = 0), unit
+ * NM_UNIT_OMEGA2 takes lambda directly, negative lo included (the full
+ * operator of NM_SELF_GRAVITY has negative eigenvalues). lambda_lo = 0 is
+ * moved to -1e-8 * lambda_max at solve time so that zero modes are inside.
+ * A slice whose negative lambda_lo lies below the estimated bottom of the
+ * spectrum widens the Chebyshev map of its run down to that edge. */
 int nm_set_interval(nm_problem* prob, double lo, double hi, nm_unit unit);
 /* Spectrum bounds of B = P_M K_eff (Lanczos with `steps` steps, FP64):
  * lam_hi = 1.01 (theta_max + |resid|), lam_lo = min(0, theta_min) - 1e-6 lam_hi

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnm.so")
-SOURCES = ["kernels.cu", "assemble.cu", "solver.cu", "api.cu", "static_scratch.cu", "mass_tma.cu", "ozaki_gemm.cu"]
+SOURCES = ["kernels.cu", "assemble.cu", "solver.cu", "api.cu", "static_scratch.cu", "mass_tma.cu", "ozaki_gemm.cu", "selfgrav.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -966,6 +966,16 @@ int assemble(nm_ctx* ctx, const nm_mesh* mesh, const nm_model* mdl, nm_problem* 
     I.n_fs = nfs;
     P->flags = mdl->flags;
     for (int d = 0; d < 3; ++d) P->Omega[d] = mdl->Omega[d];
+    if (mdl->flags & NM_SELF_GRAVITY) {
+        std::vector<int32_t> usol(n_p2, -1), uflu(n_p2, -1);
+        for (int64_t q = 0; q < n_p2; ++q) {
+            if (us[q] >= 0) usol[q] = int_of_can[us[q]];
+            if (uf[q] >= 0) uflu[q] = int_of_can[uf[q]];
+        }
+        NM_TRY(nm::build_self_gravity(P, xyz, tet, tet10.data(), mesh->region, mdl->rho, nt, usol.data(),
+                                      uflu.data(), mdl->G));
+        I.n_charges = P->sg.np;
+    }
     return NM_OK;
 }
 

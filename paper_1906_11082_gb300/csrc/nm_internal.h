@@ -103,6 +103,20 @@ struct Workspace {
     size_t bytes = 0;
 };
 
+// Self-gravitation (selfgrav.cu): charges C (points x dofs, CSR), its
+// transpose, the charge points and their inverse self distances, and the
+// point-sized scratch of one block of up to 64 columns.
+struct SelfGravity {
+    int on = 0;
+    int64_t np = 0;
+    double G = 0;
+    DevBuf pts, invR;                 // double [3 np], [np]
+    DevBuf c_rp, c_col, c_val;        // C: int64 [np + 1], int32, double
+    DevBuf t_rp, t_col, t_val;        // C^T: int64 [n + 1], int32, double
+    DevBuf q, phi;                    // double [np * 64]
+    DevBuf part;                      // partial sums of split n-body launches (small np)
+};
+
 }  // namespace nm
 
 struct nm_ctx {
@@ -123,6 +137,19 @@ int ozaki_gemm_tn(nm_ctx* ctx, cudaStream_t s, int64_t I, int64_t J, int64_t K, 
 // NN: D (I x J, row-major, ldd) = alpha X Y + beta D, X: I x K row-major, Y: K x J col-major.
 int ozaki_gemm_nn(cudaStream_t s, int64_t I, int64_t J, int64_t K, double alpha, const double* X, int64_t ldx,
                   const double* Y, int64_t ldy, double beta, double* D, int64_t ldd);
+// Self-gravitation (selfgrav.cu). usol / uflu: internal u-node of the
+// solid / fluid copy of each P2 node, -1 where the copy does not exist.
+int build_self_gravity(nm_problem* P, const double* xyz, const int32_t* tet, const int64_t* tet10,
+                       const uint8_t* region, const double* rho, int64_t nt, const int32_t* usol,
+                       const int32_t* uflu, double G);
+// Its host part: points (x, y, z per point), inverse self distances and the
+// entries (point, dof, value) of C, duplicates not summed.
+void self_gravity_host(const double* xyz, const int32_t* tet, const int64_t* tet10, const uint8_t* region,
+                       const double* rho, int64_t nt, const int32_t* usol, const int32_t* uflu,
+                       std::vector<double>& pts, std::vector<double>& invR, std::vector<int64_t>& erow,
+                       std::vector<int32_t>& ecol, std::vector<double>& eval);
+// W -= C^T S C X, X and W row-major n x b (b <= 64) in double.
+int apply_selfgrav(nm_problem* P, const double* X, int64_t ldx, double* W, int64_t ldw, int b, cudaStream_t s);
 }  // namespace nm
 
 struct nm_problem {
@@ -139,6 +166,7 @@ struct nm_problem {
     nm::DevCSR EG;     // 3x1 blocks, u x p
     nm::DevCSR EGt;    // 1x3 blocks, p x u
     nm::DevBuf g;      // double [Nu * 3] reference field at u-nodes
+    nm::SelfGravity sg;  // -C^T S C of the full operator (NM_SELF_GRAVITY)
     double Omega[3] = {0, 0, 0};
     uint32_t flags = 0;
     // slice

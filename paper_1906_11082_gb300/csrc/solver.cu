@@ -210,7 +210,12 @@ static int apply_K_t(nm_problem* P, const T* X, int64_t ldx, T* W, int64_t ldw, 
     a.ldx = ldx;
     a.W = W;
     a.ldw = ldw;
-    a.X1 = X1;
+    // with self-gravitation the fused first mass step follows the
+    // -C^T S C X correction instead of riding on the A_G product
+    const bool sg = P->sg.on != 0;
+    if (sg && sizeof(T) != sizeof(double))
+        return fail(NM_EUNSUPPORTED, "self-gravitation needs the double or mixed precision path");
+    a.X1 = sg ? nullptr : X1;
     a.ldx1 = b;
     a.dinv = m.dM;
     a.inv_theta = (T)inv_theta_M;
@@ -223,7 +228,12 @@ static int apply_K_t(nm_problem* P, const T* X, int64_t ldx, T* W, int64_t ldw, 
         a.S = Sp;
         a.lds = b;
     }
-    return launch_bsr33<T>(a, s);
+    NM_TRY(launch_bsr33<T>(a, s));
+    if (sg) {
+        NM_TRY(apply_selfgrav(P, (const double*)X, ldx, (double*)W, ldw, b, s));
+        if (X1) NM_TRY(launch_dscale<T>(3, m.Nu, b, (T)inv_theta_M, m.dM, W, ldw, X1, b, s));
+    }
+    return NM_OK;
 }
 
 // Mass-solve semi-iteration steps 2..k_M starting from x_1 in S.XA and the
@@ -460,8 +470,18 @@ static int mixed_solve(nm_problem* P, const DevCSR& A, int R, int b, int k, cons
 }
 
 // W = K_eff X in double with the pressure inverse by a refined solve.
+static int apply_K_mixed_core(nm_problem* P, const double* X, int64_t ldx, double* W, int64_t ldw, int b,
+                              int k_P, const MixScratch& S, cudaStream_t s, bool pre_split);
+
+// ... and minus C^T S C X with self-gravitation.
 static int apply_K_mixed(nm_problem* P, const double* X, int64_t ldx, double* W, int64_t ldw, int b, int k_P,
                          const MixScratch& S, cudaStream_t s, bool pre_split = false) {
+    NM_TRY(apply_K_mixed_core(P, X, ldx, W, ldw, b, k_P, S, s, pre_split));
+    return apply_selfgrav(P, X, ldx, W, ldw, b, s);
+}
+
+static int apply_K_mixed_core(nm_problem* P, const double* X, int64_t ldx, double* W, int64_t ldw, int b,
+                              int k_P, const MixScratch& S, cudaStream_t s, bool pre_split) {
     Mats<double> m = mats<double>(P);
     const bool df = P->use_df != 0;
     // pre_split: S.Th / S.Tl already hold the exact float pair of X
@@ -1247,8 +1267,15 @@ struct RRResult {
 
 // Rayleigh-Ritz of (K_eff, M) on V (n x m row-major, ld ldv, FP64). If X is
 // non-null the selected Ritz vectors are written there (n x k, ld k).
+// With sw (host, m x nw column-major: orthonormal coefficients of the
+// converged wanted Ritz vectors of p(B)) a Ritz pair inside the slice is
+// kept only if at least half of its coefficient vector lies in their span.
+// The others are spurious Ritz values of the whole basis: mixtures of
+// unconverged directions from both sides of the slice (seen with the
+// self-gravitating planet, whose spectrum has eigenvalues far below and far
+// above the slice at the same filter value).
 static int rayleigh_ritz(nm_problem* P, const double* V, int64_t ldv, int m, double lam_lo, double lam_hi,
-                         DevBuf* X, RRResult& out) {
+                         DevBuf* X, RRResult& out, const double* sw = nullptr, int nw = 0) {
     nm_ctx* ctx = P->ctx;
     cudaStream_t s = ctx->stream;
     const int64_t n = P->info.n;
@@ -1272,13 +1299,45 @@ static int rayleigh_ritz(nm_problem* P, const double* V, int64_t ldv, int m, dou
     while (i0 < m && hw[i0] < lam_lo) ++i0;
     int i1 = i0;
     while (i1 < m && hw[i1] <= lam_hi) ++i1;
-    const int k = i1 - i0;
+    int k = i1 - i0;
     out.i0 = i0;
+    const double* Ssel = H.as<double>() + (int64_t)i0 * m;   // eigenvectors, col-major m x m
+    DevBuf Skeep;
+    out.lam.clear();
+    if (sw && nw > 0 && k > 0) {
+        std::vector<double> hz((size_t)m * k);
+        NM_CUDA(cudaMemcpy(hz.data(), Ssel, hz.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        std::vector<int> keep;
+        for (int j = 0; j < k; ++j) {
+            const double* z = hz.data() + (size_t)j * m;
+            double zz = 0, pp = 0;
+            for (int r = 0; r < m; ++r) zz += z[r] * z[r];
+            for (int c = 0; c < nw; ++c) {
+                double d = 0;
+                for (int r = 0; r < m; ++r) d += sw[(size_t)c * m + r] * z[r];
+                pp += d * d;
+            }
+            if (pp >= 0.5 * zz) keep.push_back(j);
+        }
+        if ((int)keep.size() < k) {
+            std::vector<double> hk((size_t)m * keep.size());
+            for (size_t q = 0; q < keep.size(); ++q) {
+                std::copy(hz.begin() + (size_t)keep[q] * m, hz.begin() + (size_t)(keep[q] + 1) * m,
+                          hk.begin() + q * m);
+                out.lam.push_back(hw[i0 + keep[q]]);
+            }
+            k = (int)keep.size();
+            if (k > 0) {
+                NM_TRY(Skeep.alloc(hk.size() * sizeof(double)));
+                NM_CUDA(cudaMemcpy(Skeep.p, hk.data(), hk.size() * sizeof(double), cudaMemcpyHostToDevice));
+                Ssel = Skeep.as<double>();
+            }
+        }
+    }
+    if (out.lam.empty()) out.lam.assign(hw.begin() + i0, hw.begin() + i0 + k);
     out.k = k;
-    out.lam.assign(hw.begin() + i0, hw.begin() + i1);
     out.res.assign(k, 0.0);
     if (k == 0) return NM_OK;
-    const double* Ssel = H.as<double>() + (int64_t)i0 * m;   // eigenvectors, col-major m x m
     DevBuf KX, MX, lam_d, nr, nm_;
     NM_TRY(KX.alloc((size_t)n * k * sizeof(double)));
     NM_TRY(MX.alloc((size_t)n * k * sizeof(double)));
@@ -1387,9 +1446,11 @@ int spectrum_bounds(nm_problem* P, int steps, int k_M, uint64_t seed, double* la
     // spectrum, costing filter resolution exactly where slices sit; an
     // undershoot of delta only lets T_d grow to cosh(d sqrt(2 delta / e)),
     // about 1 for delta << e / d^2.
-    (void)r_lo;
+    // With self-gravitation the operator has a negative part of unknown
+    // extent (the -C^T S C term lowers the rigid and the fluid modes), so
+    // there the bottom Ritz value is moved down by its residual bound.
     const double hi = (th[m - 1] + r_hi) * 1.01;
-    const double lo = std::min(0.0, th[0]) - 1e-6 * hi;
+    const double lo = P->sg.on ? std::min(0.0, th[0] - r_lo) - 1e-6 * hi : std::min(0.0, th[0]) - 1e-6 * hi;
     *lam_lo = lo;
     *lam_hi = hi;
     P->bounds_lo = lo;
@@ -1448,7 +1509,8 @@ static int slice_init(nm_lanczos* L, SliceState& z, double lam_lo, double lam_hi
     cudaStream_t s = P->ctx->stream;
     const int64_t n = P->info.n;
     const int b = L->b, d = L->d, ldv = L->ldv;
-    z.lam_lo = lam_lo <= 0 ? -1e-8 * L->bhi : lam_lo;
+    // lambda_lo = 0 takes the zero modes in; a negative edge stays as given
+    z.lam_lo = lam_lo == 0 ? -1e-8 * L->bhi : lam_lo;
     z.lam_hi = lam_hi;
     z.gamma.resize(d + 1);
     jackson_step_coeffs(L->blo, L->bhi, z.lam_lo, z.lam_hi, d, z.gamma.data(), &L->c, &L->e);
@@ -1528,6 +1590,11 @@ int lanczos_begin(nm_problem* P, const nm_slice_opts* o, int S, const double* la
     } else {
         NM_TRY(spectrum_bounds(P, bsteps, L->k_M, bseed, &L->blo, &L->bhi));
     }
+    // A slice that starts below the estimated bottom of the spectrum widens
+    // the Chebyshev map down to its own edge: the caller expects
+    // eigenvalues there, and outside the map the filter is unbounded.
+    for (int q = 0; q < S; ++q)
+        if (lam_lo_in[q] < 0 && lam_lo_in[q] < L->blo) L->blo = lam_lo_in[q] - 1e-6 * (L->bhi - lam_lo_in[q]);
     L->st.resize(S);
     for (int q = 0; q < S; ++q)
         NM_TRY(slice_init(L.get(), L->st[q], lam_lo_in[q], lam_hi_in[q], o->start,
@@ -1660,7 +1727,12 @@ int lanczos_step(nm_lanczos* L, int* active_out) {
                     z.R = new (std::nothrow) nm_result();
                     if (!z.R) return fail(NM_ENOMEM, "host allocation failed");
                 }
-                NM_TRY(rayleigh_ritz(P, z.V.as<double>(), ldv, m, z.lam_lo, z.lam_hi, &z.R->X, z.rr));
+                // With every wanted Ritz value of p(B) converged, the slice's
+                // pairs are the pencil's Ritz pairs that lie in the span of
+                // their Ritz vectors (the top nwanted eigenvectors of T)
+                const bool conv_all = nwanted > 0 && nconv == nwanted;
+                NM_TRY(rayleigh_ritz(P, z.V.as<double>(), ldv, m, z.lam_lo, z.lam_hi, &z.R->X, z.rr,
+                                     conv_all ? Sv.data() + (size_t)(m - nwanted) * m : nullptr, nwanted));
                 bool all = z.rr.k > 0;
                 for (double r : z.rr.res) all = all && r <= L->tol;
                 if (all || last) {
@@ -1826,7 +1898,7 @@ int ritz(nm_problem* P, nm_ritz_mode mode, const double* V, int64_t ldv, int m, 
     if (!R) return fail(NM_ENOMEM, "host allocation failed");
     std::unique_ptr<nm_result> guard(R);
     if (mode == NM_RITZ_PENCIL) {
-        const double lam_lo = P->lo <= 0 ? -1e-8 * std::max(1.0, std::fabs(P->hi)) : P->lo;
+        const double lam_lo = P->lo == 0 ? -1e-8 * std::max(1.0, std::fabs(P->hi)) : P->lo;
         RRResult rr;
         NM_TRY(rayleigh_ritz(P, V, ldv, m, lam_lo, P->hi, &R->X, rr));
         R->lambda = rr.lam;

@@ -20,7 +20,7 @@ NM_OK, NM_EINVAL, NM_ENOMEM, NM_ENOTCONV, NM_ECUDA, NM_ETIMEOUT, NM_EUNSUPPORTED
 NM_F64, NM_F32, NM_MIXED = 0, 1, 2
 NM_UNIT_OMEGA, NM_UNIT_OMEGA2 = 0, 1
 NM_RITZ_PENCIL, NM_RITZ_ROTATING = 0, 1
-NM_GRAVITY, NM_CENTRIFUGAL = 1, 2
+NM_GRAVITY, NM_CENTRIFUGAL, NM_SELF_GRAVITY = 1, 2, 4
 NM_STATIC_SCRATCH_BYTES = 16 << 20     # size of the static scratch of nm_filter_apply_static
 
 EXPORTS = (
@@ -56,7 +56,7 @@ class nm_model(C.Structure):
 
 class nm_problem_info(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("nv", "nt", "n_p2", "Nu", "n", "Np", "nnz_u", "nnz_p",
-                                         "nnz_e", "n_fs")]
+                                         "nnz_e", "n_fs", "n_charges")]
 
 
 class nm_filter(C.Structure):
@@ -299,9 +299,12 @@ _cudart = _find_cudart()
 
 
 class Problem:
-    """An assembled pencil resident on the device (nm_assemble)."""
+    """An assembled pencil resident on the device (nm_assemble).
 
-    def __init__(self, ctx: Context, mesh, model, gprime=None, gravity=None):
+    self_gravity=True assembles the full operator K_eff - C^T S C (Sec. 5.2)
+    instead of the Cowling approximation."""
+
+    def __init__(self, ctx: Context, mesh, model, gprime=None, gravity=None, self_gravity=False):
         self.ctx = ctx
         self._keep = []
         xyz = np.ascontiguousarray(mesh.xyz, np.float64)
@@ -317,7 +320,7 @@ class Problem:
             gravity = model.G != 0.0 or gprime is not None
         md = nm_model(_hp(rho, C.c_double), _hp(lam, C.c_double), _hp(mu, C.c_double), _hp(N2, C.c_double),
                       _hp(gp, C.c_double), float(model.G), (C.c_double * 3)(*[float(x) for x in model.Omega]),
-                      NM_GRAVITY if gravity else 0)
+                      (NM_GRAVITY if gravity else 0) | (NM_SELF_GRAVITY if self_gravity else 0))
         h = C.c_void_p()
         _check(_lib.nm_assemble(ctx.h, C.byref(m), C.byref(md), C.byref(h)), ctx.h)
         self.h = h
