@@ -122,6 +122,7 @@ def parse(argv=None):
                     help="chunked row schedule of the semi-iteration SpMMs (threads per CTA; 0 = off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f64-leg", action="store_true")
@@ -625,8 +626,13 @@ def run_ours(args):
     mflops = mass_step_flops(info, BLOCK)
     gbs = mbytes / avg_launch_s / 1e9 if dl else None
     tfl = mflops / avg_launch_s / 1e12 if dl else None
+    # the float mass-step kernel in use: the lane-group kernel, or the
+    # union-gather row groups (option union = rows per group)
+    opts_set = dict(kv.split("=", 1) for kv in args.option)
+    uni = int(opts_set.get("union", "0"))
+    mass_kernel = "kron_union_kernel<%d>" % uni if uni else TRAFFIC_CAPTURE["kernel"]
     traffic = None
-    if (s == 4 and args.h == H_MESH and TRAFFIC_CAPTURE["kernels_cu_sha256"] == kernels_sha256()):
+    if (s == 4 and args.h == H_MESH and not uni and TRAFFIC_CAPTURE["kernels_cu_sha256"] == kernels_sha256()):
         traffic = TRAFFIC_CAPTURE["bytes"]
     if args.prec == "f64" and tfl is not None and tfl / FP64_PEAK_TFLOPS > gbs / peak_hbm:
         roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -635,7 +641,7 @@ def run_ours(args):
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": peak_hbm, "unit": "GB/s",
                 "frac": (gbs / peak_hbm) if gbs else None, "traffic": traffic,
-                "kernel": "kron_warp_kernel<double, 3, 1, 1>" if s == 8 else TRAFFIC_CAPTURE["kernel"],
+                "kernel": "kron_warp_kernel<double, 3, 1, 1>" if s == 8 else mass_kernel,
                 "peak_source": f"{peak_src} copy bandwidth"}
     roof["bytes_per_launch"] = mbytes
     roof["flops_per_launch"] = mflops
@@ -672,6 +678,11 @@ def run_ours(args):
             line["serving"] = run_serving(args, local)
         except Exception as ex:  # the serving leg must not cost the slice measurement
             line["serving"] = {"error": repr(ex)}
+    if not args.no_precision and rank == 0:
+        try:
+            line["precision"] = precision_leg(nm, local)
+        except Exception as ex:
+            line["precision"] = {"error": repr(ex)}
     if not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(args.h, args.prec, k_M, max(slice_pairs, 1),
@@ -680,6 +691,46 @@ def run_ours(args):
         except Exception as ex:
             line["cpu_baseline"] = {"error": repr(ex)}
     print(json.dumps(line))
+
+
+def precision_leg(nm, device):
+    """The error of every eigenvalue of each precision form against the FP64
+    dense oracle: one slice of the three-layer planet at h = 0.25 (the
+    stored oracle eigenvalues of tests/golden/planet_slice.json, written by
+    tests/golden/make_planet_slice.py), solved in FP64, mixed and float-filter
+    form with the same filter (degree 400, b = 8)."""
+    import torch
+    from synth.model import layered_planet
+    with open(os.path.join(ROOT, "tests", "golden", "planet_slice.json")) as f:
+        gold = json.load(f)
+    ref = np.asarray(gold["eigenvalues"])
+    mesh, model = layered_planet(h=0.25, seed=7)
+    ctx = nm.Context(device)
+    P = nm.Problem(ctx, mesh, model)
+    P.set_interval(gold["lambda_lo"], gold["lambda_hi"], unit=nm.NM_UNIT_OMEGA2)
+    out = {"workload": "layered-planet-h0.25 (%d tets, %d dof), lambda in [%.4f, %.4f], %d eigenvalues"
+                       % (mesh.nt, P.n, gold["lambda_lo"], gold["lambda_hi"], len(ref)),
+           "oracle": "dense FP64 eigh (tests/golden/planet_slice.json)", "forms": {}}
+    for name, prec, k in (("f64", nm.NM_F64, 40), ("mixed", nm.NM_MIXED, 20), ("f32_filter", nm.NM_F32, 40)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = P.lanczos_slice(block=8, degree=400, k_M=k, k_P=k, max_blocks=30, check_every=2, prec=prec, seed=2,
+                            allow_unconverged=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        lam = np.sort(r.lam)
+        entry = {"found": int(len(lam)), "seconds": dt, "blocks": int(r.info["blocks"]),
+                 "max_resid": float(r.resid.max()) if len(lam) else None}
+        if len(lam) == len(ref):
+            err = np.abs(lam - ref) / np.abs(ref)
+            entry["rel_error"] = [float(e) for e in err]
+            entry["max_rel_error"] = float(err.max())
+        else:
+            entry["count_mismatch"] = True
+        out["forms"][name] = entry
+        r.free()
+    ctx.close()
+    return out
 
 
 def gemm_case(nm, device):
