@@ -626,13 +626,8 @@ def run_ours(args):
     mflops = mass_step_flops(info, BLOCK)
     gbs = mbytes / avg_launch_s / 1e9 if dl else None
     tfl = mflops / avg_launch_s / 1e12 if dl else None
-    # the float mass-step kernel in use: the lane-group kernel, or the
-    # union-gather row groups (option union = rows per group)
-    opts_set = dict(kv.split("=", 1) for kv in args.option)
-    uni = int(opts_set.get("union", "0"))
-    mass_kernel = "kron_union_kernel<%d>" % uni if uni else TRAFFIC_CAPTURE["kernel"]
     traffic = None
-    if (s == 4 and args.h == H_MESH and not uni and TRAFFIC_CAPTURE["kernels_cu_sha256"] == kernels_sha256()):
+    if (s == 4 and args.h == H_MESH and TRAFFIC_CAPTURE["kernels_cu_sha256"] == kernels_sha256()):
         traffic = TRAFFIC_CAPTURE["bytes"]
     if args.prec == "f64" and tfl is not None and tfl / FP64_PEAK_TFLOPS > gbs / peak_hbm:
         roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -641,7 +636,7 @@ def run_ours(args):
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": peak_hbm, "unit": "GB/s",
                 "frac": (gbs / peak_hbm) if gbs else None, "traffic": traffic,
-                "kernel": "kron_warp_kernel<double, 3, 1, 1>" if s == 8 else mass_kernel,
+                "kernel": "kron_warp_kernel<double, 3, 1, 1>" if s == 8 else TRAFFIC_CAPTURE["kernel"],
                 "peak_source": f"{peak_src} copy bandwidth"}
     roof["bytes_per_launch"] = mbytes
     roof["flops_per_launch"] = mflops
