@@ -121,6 +121,12 @@ def parse(argv=None):
                          "vectors (eq. sublinear0); one JSON line")
     ap.add_argument("--rot-h", type=float, default=0.1, help="mesh size of the --rotating run")
     ap.add_argument("--rot-degree", type=int, default=800, help="filter degree of the --rotating run")
+    ap.add_argument("--heterogeneous", action="store_true",
+                    help="instead of the bench line: the rotating planet with a seeded spherical-harmonic "
+                         "perturbation (degree 20, 3%% in the solid layers) and HETERO_SLICES, 16 adjacent "
+                         "slices solved as one batched run (b = 4 each, one 64-column recurrence), then the "
+                         "rotating projection of all their Ritz vectors; one JSON line")
+    ap.add_argument("--het-degree", type=int, default=3000, help="filter degree of the --heterogeneous run")
     ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
                     help="problem option (nm_set_option), repeatable")
     ap.add_argument("--chunk", type=int, default=None,
@@ -491,6 +497,9 @@ def run_ours(args):
     if args.rotating:
         rotating_case(nm, local, args.rot_h, args.rot_degree)
         return
+    if args.heterogeneous:
+        rotating_case(nm, local, args.rot_h, args.het_degree, b=4, slices=HETERO_SLICES, lateral=0.03)
+        return
     w = workload(args.h)
     ctx = nm.Context(local)
     torch.cuda.synchronize()
@@ -792,9 +801,11 @@ def selfgrav_case(nm, device, h, b=32, reps=5):
 # Four adjacent slices of the rotating planet's seismic band (angular
 # frequency), about 200 eigenpairs together.
 ROTATING_SLICES = [(4.0, 5.0), (5.0, 6.0), (6.0, 7.0), (7.0, 8.0)]
+# Sixteen adjacent slices of width 0.25 over the same band.
+HETERO_SLICES = [(4.0 + 0.25 * i, 4.25 + 0.25 * i) for i in range(16)]
 
 
-def rotating_case(nm, device, h, degree, b=16):
+def rotating_case(nm, device, h, degree, b=16, slices=None, lateral=0.0):
     """The rotating layered planet: the slices solved in one batched run
     (their blocks filtered as one 64-column recurrence, the mixed form), then
     the rotating reduction (eq. sublinear0) on all their Ritz vectors at
@@ -802,14 +813,15 @@ def rotating_case(nm, device, h, degree, b=16):
     eigenpairs/s counts the pencil pairs with residual <= 1e-6."""
     import torch
     from synth.model import OMEGA_EARTH_NONDIM, layered_planet
-    mesh, model = layered_planet(h=h, seed=2, omega=OMEGA_EARTH_NONDIM)
+    slices = slices or ROTATING_SLICES
+    mesh, model = layered_planet(h=h, seed=2, omega=OMEGA_EARTH_NONDIM, lateral=lateral, lateral_lmax=20)
     ctx = nm.Context(device)
     t0 = time.perf_counter()
     P = nm.Problem(ctx, mesh, model)
     torch.cuda.synchronize()
     t_asm = time.perf_counter() - t0
     t0 = time.perf_counter()
-    res = P.lanczos_multi(ROTATING_SLICES, block=b, degree=degree, k_M=20, k_P=20, max_blocks=40, check_every=2,
+    res = P.lanczos_multi(slices, block=b, degree=degree, k_M=20, k_P=20, max_blocks=40, check_every=2,
                           prec=nm.NM_MIXED, seed=SEED, allow_unconverged=True)
     torch.cuda.synchronize()
     t_lanczos = time.perf_counter() - t0
@@ -817,14 +829,16 @@ def rotating_case(nm, device, h, degree, b=16):
     lam_e = np.concatenate([r.lam for r in res])
     t0 = time.perf_counter()
     Xe = torch.cat([r.vectors() for r in res], dim=1).contiguous()
-    P.set_interval(ROTATING_SLICES[0][0], ROTATING_SLICES[-1][1])
+    P.set_interval(slices[0][0], slices[-1][1])
     rot = P.ritz(Xe, mode=nm.NM_RITZ_ROTATING, lam_e=lam_e)
     torch.cuda.synchronize()
     t_rot = time.perf_counter() - t0
     print(json.dumps({
-        "workload": "rotating-layered-planet-h%g" % h, "tets": int(mesh.nt), "dof": int(P.n),
-        "pressure_dof": int(P.Np), "omega_rotation": OMEGA_EARTH_NONDIM, "slices_omega": ROTATING_SLICES,
-        "block": b, "degree": degree, "filter_prec": "mixed", "batched_columns": b * len(ROTATING_SLICES),
+        "workload": ("rotating-heterogeneous-planet-h%g" if lateral else "rotating-layered-planet-h%g") % h,
+        "lateral_perturbation": {"amplitude": lateral, "lmax": 20} if lateral else None,
+        "tets": int(mesh.nt), "dof": int(P.n),
+        "pressure_dof": int(P.Np), "omega_rotation": OMEGA_EARTH_NONDIM, "slices_omega": slices,
+        "block": b, "degree": degree, "filter_prec": "mixed", "batched_columns": b * len(slices),
         "eigenpairs": int(sum(good)),
         "per_slice": [{"pairs": g, "found": len(r.lam), "blocks": int(r.info["blocks"]),
                        "max_resid": float(r.resid.max()) if len(r.lam) else None} for g, r in zip(good, res)],

@@ -288,6 +288,7 @@ def lanczos_slice(op: Operator, lam_lo, lam_hi, d, b, max_blocks, seed=0,
     Tcols = []
     info = dict(blocks=0, tau=tau, c=c, e=e, bounds=bounds)
     lam = X = res = None
+    empty_checks = 0
     for j in range(max_blocks):
         Vj = basis[-1]
         W = filter_apply(op, gamma, c, e, Vj)
@@ -317,6 +318,16 @@ def lanczos_slice(op: Operator, lam_lo, lam_hi, d, b, max_blocks, seed=0,
             if len(lam) and np.all(res <= tol):
                 info['m'] = m
                 return lam, X, res, info
+            # empty slice: all wanted Ritz values of p(B) converged (they
+            # belong to eigenvalues outside the slice; one inside would have
+            # p >= tau) and no pair in the slice, at two consecutive checks
+            # from the fourth block on
+            empty_checks = empty_checks + 1 if len(lam) == 0 else 0
+            if empty_checks >= 2 and j + 1 >= 4:
+                info['m'] = m
+                return lam, X, res, info
+        elif (j + 1) % check_every == 0:
+            empty_checks = 0
     Vall = np.concatenate(basis[:-1], axis=1)
     lam, X, res = rayleigh_ritz(op, Vall, lam_lo, lam_hi)
     info['m'] = Vall.shape[1]

@@ -1473,6 +1473,7 @@ struct SliceState {
     int blocks = 0, m_used = 0;
     bool active = true, converged = false, ok = true, taken = false;
     int nwanted = 0, nconv = 0;   // at the last block step
+    int empty_checks = 0;         // consecutive converged checks that found no pair in the slice
     RRResult rr;
     nm_result* R = nullptr;
 };
@@ -1735,6 +1736,13 @@ int lanczos_step(nm_lanczos* L, int* active_out) {
                                      conv_all ? Sv.data() + (size_t)(m - nwanted) * m : nullptr, nwanted));
                 bool all = z.rr.k > 0;
                 for (double r : z.rr.res) all = all && r <= L->tol;
+                // An empty slice: every wanted Ritz value of p(B) has converged
+                // (all of them belong to eigenvalues outside the slice) and no
+                // pencil pair lies in the slice, at two consecutive checks
+                // from the fourth block on. An eigenvalue inside the slice has
+                // p >= tau, so it would be among the wanted ones.
+                z.empty_checks = conv_all && z.rr.k == 0 ? z.empty_checks + 1 : 0;
+                if (z.empty_checks >= 2 && j + 1 >= 4) all = true;
                 if (all || last) {
                     z.converged = all;
                     z.active = false;

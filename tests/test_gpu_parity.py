@@ -372,6 +372,19 @@ def test_empty_slice_reports_not_converged(nm, ball):
     assert len(res.lam) == 0
 
 
+def test_empty_slice_converges_early(nm, ball):
+    """A slice in a gap of the dense spectrum ([8, 10.5] in lambda on this
+    mesh) with a filter sharp enough to converge the eigenvalues around it:
+    the run reports the slice converged with no pair before its block limit."""
+    w, S, P = ball
+    lam = eig.all_eigs(*eig.pencil_dense(S))[0]
+    assert not ((lam >= 8.0) & (lam <= 10.5)).any()
+    P.set_interval(8.0, 10.5, unit=nm.NM_UNIT_OMEGA2)
+    res = P.lanczos_slice(block=4, degree=200, k_M=30, k_P=30, max_blocks=16, seed=1)
+    assert len(res.lam) == 0 and res.info["blocks"] < 16
+    res.free()
+
+
 def test_invalid_block_width(nm, ball):
     _, S, P = ball
     X = torch.zeros((S.n, 65), dtype=torch.float64, device=DEV)

@@ -512,6 +512,18 @@ def test_lanczos_slice_matches_dense(ball):
     assert r2.max() <= 1e-6
 
 
+def test_lanczos_empty_slice_stops_early(ball):
+    """A slice inside a gap of the dense spectrum (no eigenvalue in [8, 10.5]
+    on this mesh): every wanted Ritz value of p(B) belongs to an eigenvalue
+    outside it, so once they have converged the run returns no pair before
+    its block limit."""
+    w, S, K, M, lam, _ = ball
+    assert not ((lam >= 8.0) & (lam <= 10.5)).any()
+    op = filtlan.Operator(S, k_M=30, k_P=30)
+    got, X, res, info = filtlan.lanczos_slice(op, 8.0, 10.5, 200, 4, 16, seed=1)
+    assert len(got) == 0 and info["blocks"] < 16
+
+
 # ------------------------------------------------------------ rotation
 def _ball_T2(h, omega):
     mesh, model = homogeneous_ball(h=h, seed=1)
