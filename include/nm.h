@@ -331,8 +331,12 @@ int nm_filter_apply_static(nm_problem* prob, const nm_filter* f, const double* Y
 
 /* Filtered block Lanczos for every eigenpair with lambda in the interval
  * set by nm_set_interval (Sec. 6.2), followed by an FP64 Rayleigh-Ritz of
- * the pencil and FP64 residuals. NM_ENOTCONV if max_blocks is reached
- * before every eigenpair in the slice passes tol (the result is still
+ * the pencil and FP64 residuals. The slice has converged when every Ritz
+ * value of the filtered operator above the threshold has converged and
+ * the slice's pencil pairs in their span pass tol; it is converged and
+ * empty (k = 0) when, at two consecutive checks from the fourth block on,
+ * those Ritz values have converged and no pair lies in the slice.
+ * NM_ENOTCONV if max_blocks is reached first (the result is still
  * returned). */
 int nm_lanczos_slice(nm_problem* prob, const nm_slice_opts* opts, nm_result** out);
 
