@@ -50,7 +50,7 @@ enum {
     NM_ENOTCONV = 3,      /* solver stopped without converging              */
     NM_ECUDA = 4,         /* a CUDA / cuBLAS / cuSOLVER call failed          */
     NM_ETIMEOUT = 5,      /* a bounded device wait ran out                  */
-    NM_EUNSUPPORTED = 6   /* option not supported by this build              */
+    NM_EUNSUPPORTED = 6   /* option not supported by the library            */
 };
 
 /* NM_F64: every step in double. NM_F32: the whole filter recurrence in
